@@ -1,0 +1,233 @@
+/*
+ * spmttkrp.h -- C ABI of the GB300 (sm_103a) sparse MTTKRP / CPD-ALS library.
+ *
+ * The library computes, for an N-mode sparse tensor X in COO form and dense
+ * factor matrices Y_0..Y_{N-1} (I_w x R), the sparse MTTKRP along any mode d
+ *
+ *     M_d(i, r) = sum over nonzeros x with c_d(x) = i of
+ *                 val(x) * prod_{w != d} Y_w(c_w(x), r)
+ *
+ * (Eq. 1 of "Accelerating Sparse MTTKRP for Small Tensor Decomposition on
+ * GPU", written elementwise in its Sec. II-A6 and generalised to N modes in
+ * its Algorithm 2), and CP-ALS sweeps built on it (Sec. II-A5).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Pointers marked "device" are CUDA device pointers of the current device;
+ *   pointers marked "host" are ordinary host memory.
+ * - Matrices are row-major with leading dimension R (element (i, r) at
+ *   i*R + r).  Indices are int32, values FP32.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Every call is stream-ordered and returns without waiting for
+ *   the GPU, except spmttkrp_plan, which synchronises `stream` once to read
+ *   its validation flag.
+ * - Errors are returned as spm_status; nothing is thrown across the ABI and
+ *   no call aborts the process.  Device-side checks set flags that the host
+ *   reads; no kernel traps.  A failing call leaves caller-owned outputs in an
+ *   unspecified state.
+ * - The library never calls into any CPU fallback: every step runs in its own
+ *   CUDA kernels.  Loading it on a machine without a CUDA device is fine;
+ *   calls then return SPM_ERR_CUDA.
+ */
+#ifndef SPMTTKRP_H_
+#define SPMTTKRP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spmttkrp_plan_s *spmttkrp_plan_t;
+
+typedef enum {
+  SPM_OK = 0,
+  SPM_ERR_INVALID_ARG = 1,        /* bad count, pointer, mode, rank or flag   */
+  SPM_ERR_INDEX_OUT_OF_RANGE = 2, /* some idx[w][k] < 0 or >= dims[w]         */
+  SPM_ERR_OOM = 3,                /* a device allocation failed               */
+  SPM_ERR_CUDA = 4,               /* a CUDA runtime call failed               */
+  SPM_ERR_NUMERIC = 5,            /* ALS system not positive definite / NaN   */
+  SPM_ERR_TIMEOUT = 6,            /* a bounded device-side wait gave up       */
+  SPM_ERR_UNSUPPORTED = 7         /* valid request outside what is built      */
+} spm_status;
+
+/* ---- plan flags ---------------------------------------------------------- */
+/* Storage type of the factor matrices passed to spmttkrp_run/cpd_als_step.
+ * BF16 halves the bytes gathered per nonzero; accumulation stays FP32. */
+#define SPM_FACTOR_FP32 0x0u
+#define SPM_FACTOR_BF16 0x1u
+#define SPM_FACTOR_MASK 0x1u
+
+/* Partitioning policy of the nonzeros of each mode copy across the kappa
+ * thread-block partitions (Sec. III-B) and, inside each partition, into
+ * NU = SPM_UNITS_PER_PARTITION(R) work units that the block's warps take in
+ * turn:
+ *  BALANCED (default) the copy (in key order) is cut into kappa * NU
+ *           contiguous work units of equal cost, where a
+ *           nonzero costs 1, plus SPM_ROW_COST if it is the first nonzero of
+ *           its output row (a row change is what the kernel pays for beyond
+ *           streaming).  Unit j starts at the smallest copy position k
+ *           with C(k) * P >= j * C(nnz), C(k) = k + SPM_ROW_COST * (rows that
+ *           start before k), P = kappa * NU.  Partition z is units
+ *           z*NU .. (z+1)*NU-1.  This keeps the
+ *           equal-nnz shape of Scheme 2 while accounting for the sparsity of
+ *           the output mode (row boundaries).
+ *  SCHEME2  equal distribution of nonzeros (Sec. III-B2): partition z holds
+ *           copy positions [floor(z*nnz/kappa), floor((z+1)*nnz/kappa)).
+ *  SCHEME1  equal distribution of output indices (Sec. III-B1): rows with at
+ *           least one nonzero are ordered by degree (descending, ties by
+ *           index) and dealt cyclically to the partitions; the copy is then
+ *           ordered by partition, so no row spans two partitions.
+ *  ADAPTIVE the paper's rule per mode: SCHEME1 when I_d >= kappa, else
+ *           SCHEME2 (Sec. III-B).
+ * With SCHEME1/SCHEME2 each partition is split into work units of equal
+ * nonzero count: unit w of partition z starts at
+ * off[z] + floor((off[z+1] - off[z]) * w / NU).
+ * Rows that straddle units or partitions are combined deterministically. */
+#define SPM_POLICY_BALANCED (0u << 4)
+#define SPM_POLICY_SCHEME2 (1u << 4)
+#define SPM_POLICY_SCHEME1 (2u << 4)
+#define SPM_POLICY_ADAPTIVE (3u << 4)
+#define SPM_POLICY_MASK (0xFu << 4)
+
+/* work units per partition for rank R: 4096 / R clamped to [16, 128] */
+#define SPM_UNITS_PER_PARTITION(R) \
+  ((4096 / (R)) < 16 ? 16 : ((4096 / (R)) > 128 ? 128 : (4096 / (R))))
+#define SPM_ROW_COST 16 /* extra cost of a row start, in nonzeros */
+
+/* Number of partitions kappa.  0 (default) = the device's SM count, one
+ * thread block per SM (Sec. III-B: one partition per streaming
+ * multiprocessor).  Any value 1..65535 may be forced, e.g. for tests. */
+#define SPM_KAPPA(k) (((uint32_t)(k) & 0xFFFFu) << 16)
+#define SPM_KAPPA_OF(flags) (((uint32_t)(flags) >> 16) & 0xFFFFu)
+
+/* Limits of this build. */
+#define SPM_MAX_MODES 7
+#define SPM_MAX_RANK 256
+
+/* ---- plan ---------------------------------------------------------------- */
+
+/* Build the mode-specific tensor copies and their partitions
+ * (Sec. III-C: one COO copy per output mode; Sec. III-B: the partitions).
+ *
+ *  out      host; receives the plan handle (NULL on failure).
+ *  nmodes   N, 2 <= N <= SPM_MAX_MODES.
+ *  dims     host int64[N]; 1 <= dims[w] < 2^31.
+ *  nnz      number of nonzeros, 0 <= nnz < 2^31 - 2^20.
+ *  idx      host array of N device pointers, idx[w] = int32[nnz] mode-w
+ *           coordinates.  Duplicate coordinates are allowed and are summed
+ *           (MTTKRP is linear in the values).
+ *  vals     device float[nnz].
+ *  rank     R, 1 <= R <= SPM_MAX_RANK; factors passed later must have R
+ *           columns.
+ *  flags    SPM_FACTOR_*, SPM_POLICY_*, SPM_KAPPA(k), or-ed.
+ *  stream   cudaStream_t as void*.
+ *
+ * For every mode d the copy holds the nonzeros ordered by the key
+ * (c_d, then c_w for w != d in ascending w, then input position); with
+ * SCHEME1 the copy is further ordered by partition id first (stable).
+ * All indices are checked on the device: any index outside [0, dims[w])
+ * yields SPM_ERR_INDEX_OUT_OF_RANGE and no plan.
+ * Ownership: the plan copies everything it needs, so idx/vals may be freed
+ * once this call returns.  The plan owns all its device memory until
+ * spmttkrp_plan_destroy. */
+spm_status spmttkrp_plan(spmttkrp_plan_t *out, int nmodes,
+                         const int64_t *dims, int64_t nnz,
+                         const int32_t *const *idx, const float *vals,
+                         int rank, uint32_t flags, void *stream);
+
+/* Device bytes held by the plan (all copies, permutations, partitions and
+ * its workspace) -- the "total memory consumption" of Sec. V-C and the
+ * admission figure of a serving loop.  `bytes` is host. */
+spm_status spmttkrp_plan_bytes(spmttkrp_plan_t plan, size_t *bytes);
+
+/* Input positions of the nonzeros of the mode-`mode` copy, in copy order
+ * (the permutation pi_d of Sec. III-B2's ordering).  perm: device
+ * int64[nnz]. */
+spm_status spmttkrp_plan_permutation(spmttkrp_plan_t plan, int mode,
+                                     int64_t *perm, void *stream);
+
+/* Partition offsets of the mode-`mode` copy: off[z]..off[z+1] are the copy
+ * positions of partition B_{d,z} (Algorithm 1), z = 0..kappa-1.
+ * off: device int64[kappa+1].  *kappa_out (host, may be NULL) = kappa. */
+spm_status spmttkrp_plan_partition(spmttkrp_plan_t plan, int mode,
+                                   int64_t *off, int *kappa_out,
+                                   void *stream);
+
+/* Policy used for mode `mode` after ADAPTIVE is resolved: 1 = Scheme 1,
+ * 2 = Scheme 2 (Sec. III-B), 0 = cost-balanced.  `scheme` is host. */
+spm_status spmttkrp_plan_scheme(spmttkrp_plan_t plan, int mode, int *scheme);
+
+/* Work-unit offsets of the mode-`mode` copy: off[j]..off[j+1] are the copy
+ * positions of work unit j, j = 0..kappa*NU-1 with NU =
+ * SPM_UNITS_PER_PARTITION(rank) (see the policy flags above).
+ * off: device int64[kappa*NU+1]. */
+spm_status spmttkrp_plan_work_units(spmttkrp_plan_t plan, int mode, int64_t *off,
+                                    void *stream);
+
+/* Release the plan and all its device memory (stream-ordered frees after a
+ * device synchronisation).  NULL is ignored. */
+void spmttkrp_plan_destroy(spmttkrp_plan_t plan);
+
+/* ---- MTTKRP -------------------------------------------------------------- */
+
+/* M_mode = X_(mode) (Khatri-Rao product of the other factors), Eq. 1 /
+ * Algorithm 1 for one mode.
+ *
+ *  factors  host array of N device pointers, factors[w] = I_w x R row-major,
+ *           float or bf16 as the plan's SPM_FACTOR_* flag says; factors[mode]
+ *           is not read and may be NULL.  Each must be 16-byte aligned.
+ *  out      device float[I_mode * R], overwritten (rows without nonzeros are
+ *           written as zero).  Must not alias a factor.
+ *  stream   cudaStream_t as void*.
+ *
+ * Accumulation is FP32; the summation order is fixed by the plan, so repeated
+ * calls give bitwise identical results.  Calls on one plan that overlap on
+ * the GPU (different streams, no ordering) race on the plan's workspace. */
+spm_status spmttkrp_run(spmttkrp_plan_t plan, int mode,
+                        const void *const *factors, float *out, void *stream);
+
+/* ---- CPD-ALS --------------------------------------------------------------- */
+
+/* One CP-ALS sweep over modes 0..N-1 in order (Sec. II-A5), Gauss-Seidel:
+ * for each d,
+ *   M      = spMTTKRP_d(factors)                     (the plan's kernels)
+ *   V      = Hadamard over w != d of (Y_w^T Y_w)     (R x R, FP64)
+ *   Z      = M V^{-1}, through the FP64 Cholesky factor of V
+ *   lambda = column 2-norms of Z;  Y_d = Z diag(1/lambda) (columns with
+ *            lambda_r = 0 are left as they are), stored as FP32 or BF16.
+ * After the last mode the fit 1 - |X - Xhat|_F / |X|_F is evaluated from
+ * |X|^2, lambda, the Grams and the last mode's M (Kolda & Bader).
+ *
+ *  factors  host array of N device pointers, updated in place.
+ *  lambda   device double[R], receives the weights of the last mode.
+ *  fit      device double[1] or NULL.
+ *  stream   cudaStream_t as void*.
+ *
+ * The Gram of each factor is cached in the plan and refreshed after its
+ * update; the cache is (re)built from `factors` on the first call and
+ * whenever the factor pointers change.  If V is not numerically positive
+ * definite the sweep stops at that mode, later calls return
+ * SPM_ERR_NUMERIC, and spmttkrp_plan_status reports it (the check is
+ * device-side, so it is seen at the next synchronising call). */
+spm_status cpd_als_step(spmttkrp_plan_t plan, void *const *factors,
+                        double *lambda, double *fit, void *stream);
+
+/* Synchronise `stream` and return the plan's sticky device-side error
+ * (SPM_OK, SPM_ERR_NUMERIC or SPM_ERR_TIMEOUT), then clear it. */
+spm_status spmttkrp_plan_status(spmttkrp_plan_t plan, void *stream);
+
+/* ---- misc ------------------------------------------------------------------ */
+
+/* Static, never-NULL description of a status code. */
+const char *spm_status_string(spm_status s);
+
+/* Number of SMs of the current device (the default kappa), or -1. */
+int spm_device_sm_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPMTTKRP_H_ */

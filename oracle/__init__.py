@@ -16,6 +16,8 @@ Which passage each routine follows:
 * :func:`mode_permutation` -- Sec. III-B2 (nonzeros ordered by the output-mode
   index); ties by the other modes in ascending mode order, then by position.
 * :func:`partition_equal` -- Sec. III-B2 (kappa equal-size partitions).
+* :func:`partition_balanced` -- Sec. III-B2's ordered nonzeros cut into
+  equal-cost work units (nonzeros plus a charge per output-row start).
 * :func:`partition_scheme1` -- Sec. III-B1 (degree-ordered cyclic deal).
 * :func:`adaptive_policy` -- Sec. III-B (I_d >= kappa selects Scheme 1).
 * :func:`cpd_als` -- Sec. II-A5 (CP-ALS over Eq. 1), standard normal-equation
@@ -74,6 +76,7 @@ def _load():
                                                i64, P, P]
             lib.oracle_mode_permutation.argtypes = [i32, i64, P, i32, P]
             lib.oracle_partition_equal.argtypes = [i64, i32, P]
+            lib.oracle_partition_balanced.argtypes = [i64, P, i64, i64, P]
             lib.oracle_partition_scheme1.argtypes = [i32, P, i64, P, i32, i32,
                                                      P, P, P]
             lib.oracle_cpd_als.argtypes = [i32, P, i64, P, P, i32, P, i32, i32,
@@ -158,6 +161,33 @@ def partition_equal(nnz, kappa):
     _check(lib.oracle_partition_equal(int(nnz), int(kappa), off.ctypes.data),
            "oracle_partition_equal")
     return off
+
+
+def partition_balanced(idx, mode, parts, row_cost=16, perm=None):
+    """Cost-balanced work-unit offsets (int64[parts+1]) of the mode copy:
+    a nonzero costs 1 plus `row_cost` if it starts its output row."""
+    lib = _load()
+    idx = _idx_list(idx)
+    if perm is None:
+        perm = mode_permutation(idx, mode)
+    rows = np.ascontiguousarray(idx[mode][perm], dtype=np.int32)
+    off = np.empty(int(parts) + 1, dtype=np.int64)
+    _check(lib.oracle_partition_balanced(int(rows.size), rows.ctypes.data, int(parts),
+                                         int(row_cost), off.ctypes.data),
+           "oracle_partition_balanced")
+    return off
+
+
+def units_from_partitions(off, units):
+    """Work units of a partition vector: unit w of partition z starts at
+    off[z] + floor((off[z+1] - off[z]) * w / units)."""
+    off = np.asarray(off, dtype=np.int64)
+    out = []
+    for z in range(off.size - 1):
+        for w in range(units):
+            out.append(off[z] + ((off[z + 1] - off[z]) * w) // units)
+    out.append(off[-1])
+    return np.asarray(out, dtype=np.int64)
 
 
 def partition_scheme1(dims, idx, mode, kappa):

@@ -21,6 +21,10 @@
  *   oracle_partition_equal
  *                        Sec. III-B2: kappa equal-size partitions of the
  *                        ordered nonzeros, offsets floor(z*nnz/kappa).
+ *   oracle_partition_balanced
+ *                        Sec. III-B2's ordered nonzeros cut into equal-cost
+ *                        pieces, a nonzero costing 1 plus a fixed extra for
+ *                        the first nonzero of each output row.
  *   oracle_partition_scheme1
  *                        Sec. III-B1: rows ordered by degree (descending,
  *                        ties by index), dealt cyclically to kappa partitions,
@@ -176,6 +180,30 @@ int oracle_partition_equal(int64_t nnz, int kappa, int64_t *off) {
     /* exact floor(z*nnz/kappa) without overflow for nnz < 2^62/kappa */
     off[z] = (int64_t)(((__int128)z * nnz) / kappa);
   }
+  return ORACLE_OK;
+}
+
+/* Cost-balanced work units over a copy: rows[k] is the output index of the
+ * k-th nonzero in copy order.  A nonzero costs 1, plus row_cost if it starts
+ * its row (k == 0 or rows[k] != rows[k-1]).  With C(k) the cost of positions
+ * before k and P units, unit j starts at the smallest k with
+ * C(k) * P >= j * C(nnz).  off has P + 1 entries. */
+int oracle_partition_balanced(int64_t nnz, const int32_t *rows, int64_t parts,
+                              int64_t row_cost, int64_t *off) {
+  if (parts < 1 || nnz < 0 || row_cost < 0) return ORACLE_ERR_ARG;
+  int64_t *C = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz + 1));
+  if (!C) return ORACLE_ERR_NOMEM;
+  C[0] = 0;
+  for (int64_t k = 0; k < nnz; ++k) {
+    int start = (k == 0) || rows[k] != rows[k - 1];
+    C[k + 1] = C[k] + 1 + (start ? row_cost : 0);
+  }
+  int64_t k = 0;
+  for (int64_t j = 0; j <= parts; ++j) {
+    while (C[k] * parts < j * C[nnz]) ++k;
+    off[j] = k;
+  }
+  free(C);
   return ORACLE_OK;
 }
 

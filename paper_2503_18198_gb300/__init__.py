@@ -1,0 +1,16 @@
+"""GB300-native (sm_103a) sparse MTTKRP along every mode of a small N-mode
+COO tensor, and CP-ALS on top of it.
+
+The computation lives in hand-written CUDA kernels behind the C ABI of
+``include/spmttkrp.h`` (library ``_lib/libspmttkrp.so``); :mod:`.binding` is
+a thin ctypes layer over it that takes PyTorch CUDA tensors and streams.
+"""
+from .binding import (SPM_FACTOR_BF16, SPM_FACTOR_FP32, SPM_KAPPA,  # noqa: F401
+                      SPM_POLICY_ADAPTIVE, SPM_POLICY_BALANCED,
+                      SPM_POLICY_SCHEME1, SPM_POLICY_SCHEME2, SPM_ROW_COST,
+                      SPM_UNITS_PER_PARTITION, Plan, SpmError, cpd_als_step, load,
+                      spm_device_sm_count, spm_status_string, spmttkrp_plan,
+                      spmttkrp_plan_bytes, spmttkrp_plan_destroy,
+                      spmttkrp_plan_partition, spmttkrp_plan_permutation,
+                      spmttkrp_plan_scheme, spmttkrp_plan_status,
+                      spmttkrp_plan_work_units, spmttkrp_run)

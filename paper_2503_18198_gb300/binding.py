@@ -1,0 +1,235 @@
+"""Thin ctypes binding of the C ABI in include/spmttkrp.h.
+
+Argument marshalling only: every computation runs in the CUDA library
+(_lib/libspmttkrp.so).  There is no fallback of any kind -- if the library is
+missing, :func:`load` raises.  PyTorch supplies device memory and the current
+stream; the functions below keep the C names and argument order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+SPM_OK = 0
+STATUS = {0: "SPM_OK", 1: "SPM_ERR_INVALID_ARG", 2: "SPM_ERR_INDEX_OUT_OF_RANGE",
+          3: "SPM_ERR_OOM", 4: "SPM_ERR_CUDA", 5: "SPM_ERR_NUMERIC",
+          6: "SPM_ERR_TIMEOUT", 7: "SPM_ERR_UNSUPPORTED"}
+
+SPM_FACTOR_FP32 = 0x0
+SPM_FACTOR_BF16 = 0x1
+SPM_POLICY_BALANCED = 0 << 4
+SPM_POLICY_SCHEME2 = 1 << 4
+SPM_POLICY_SCHEME1 = 2 << 4
+SPM_POLICY_ADAPTIVE = 3 << 4
+SPM_ROW_COST = 16
+
+
+def SPM_UNITS_PER_PARTITION(R: int) -> int:
+    u = 4096 // int(R)
+    return 16 if u < 16 else (128 if u > 128 else u)
+SPM_MAX_MODES = 7
+SPM_MAX_RANK = 256
+
+
+def SPM_KAPPA(k: int) -> int:
+    return (int(k) & 0xFFFF) << 16
+
+
+class SpmError(RuntimeError):
+    def __init__(self, status: int, what: str, text: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({text})")
+
+
+_lib = None
+
+#: exported symbols declared in include/spmttkrp.h
+SYMBOLS = ("spmttkrp_plan", "spmttkrp_plan_bytes", "spmttkrp_plan_permutation",
+           "spmttkrp_plan_partition", "spmttkrp_plan_work_units", "spmttkrp_plan_scheme",
+           "spmttkrp_plan_destroy", "spmttkrp_run", "cpd_als_step",
+           "spmttkrp_plan_status", "spm_status_string", "spm_device_sm_count")
+
+
+def library_path() -> str:
+    return _build.so_path()
+
+
+def load(build_if_missing: bool = False):
+    """Load libspmttkrp.so (building it first only if asked).  Raises if the
+    library is absent: the package has no other implementation."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(
+                f"CUDA library {path} is missing; run __graft_entry__.build() "
+                "(or python -m paper_2503_18198_gb300._build) first")
+        path = _build.build()
+    lib = ctypes.CDLL(path)
+    P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint32
+    lib.spmttkrp_plan.argtypes = [P, i32, P, i64, P, P, i32, u32, P]
+    lib.spmttkrp_plan.restype = i32
+    lib.spmttkrp_plan_bytes.argtypes = [P, P]
+    lib.spmttkrp_plan_bytes.restype = i32
+    lib.spmttkrp_plan_permutation.argtypes = [P, i32, P, P]
+    lib.spmttkrp_plan_permutation.restype = i32
+    lib.spmttkrp_plan_partition.argtypes = [P, i32, P, P, P]
+    lib.spmttkrp_plan_partition.restype = i32
+    lib.spmttkrp_plan_work_units.argtypes = [P, i32, P, P]
+    lib.spmttkrp_plan_work_units.restype = i32
+    lib.spmttkrp_plan_scheme.argtypes = [P, i32, P]
+    lib.spmttkrp_plan_scheme.restype = i32
+    lib.spmttkrp_plan_destroy.argtypes = [P]
+    lib.spmttkrp_plan_destroy.restype = None
+    lib.spmttkrp_run.argtypes = [P, i32, P, P, P]
+    lib.spmttkrp_run.restype = i32
+    lib.cpd_als_step.argtypes = [P, P, P, P, P]
+    lib.cpd_als_step.restype = i32
+    lib.spmttkrp_plan_status.argtypes = [P, P]
+    lib.spmttkrp_plan_status.restype = i32
+    lib.spm_status_string.argtypes = [i32]
+    lib.spm_status_string.restype = ctypes.c_char_p
+    lib.spm_device_sm_count.argtypes = []
+    lib.spm_device_sm_count.restype = i32
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != SPM_OK:
+        text = load().spm_status_string(status).decode()
+        raise SpmError(status, what, text)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptrs(tensors):
+    return (ctypes.c_void_p * len(tensors))(
+        *[t.data_ptr() if t is not None else 0 for t in tensors])
+
+
+class Plan:
+    """Owns an spmttkrp_plan_t; destroyed with the object or by destroy()."""
+
+    def __init__(self, handle: ctypes.c_void_p, nmodes: int, dims, nnz: int,
+                 rank: int, flags: int):
+        self.handle = handle
+        self.nmodes = nmodes
+        self.dims = tuple(int(d) for d in dims)
+        self.nnz = int(nnz)
+        self.rank = int(rank)
+        self.flags = int(flags)
+
+    @property
+    def bf16(self) -> bool:
+        return bool(self.flags & SPM_FACTOR_BF16)
+
+    def destroy(self):
+        if self.handle:
+            load().spmttkrp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def spm_device_sm_count() -> int:
+    return int(load().spm_device_sm_count())
+
+
+def spm_status_string(status: int) -> str:
+    return load().spm_status_string(int(status)).decode()
+
+
+def spmttkrp_plan(dims, idx, vals, rank: int, flags: int = 0, stream=None) -> Plan:
+    """idx: N int32 CUDA tensors [nnz]; vals: float32 CUDA tensor [nnz]."""
+    lib = load()
+    N = len(dims)
+    nnz = int(vals.numel())
+    dims_a = (ctypes.c_int64 * N)(*[int(d) for d in dims])
+    handle = ctypes.c_void_p()
+    st = lib.spmttkrp_plan(ctypes.byref(handle), N, dims_a, nnz, _ptrs(list(idx)),
+                           ctypes.c_void_p(vals.data_ptr() if nnz else 0), int(rank),
+                           int(flags) & 0xFFFFFFFF, _stream(stream))
+    _check(st, "spmttkrp_plan")
+    return Plan(handle, N, dims, nnz, rank, flags)
+
+
+def spmttkrp_plan_bytes(plan: Plan) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().spmttkrp_plan_bytes(plan.handle, ctypes.byref(out)), "spmttkrp_plan_bytes")
+    return int(out.value)
+
+
+def spmttkrp_plan_permutation(plan: Plan, mode: int, perm, stream=None):
+    """perm: int64 CUDA tensor [nnz], filled in copy order."""
+    _check(load().spmttkrp_plan_permutation(plan.handle, int(mode),
+                                            ctypes.c_void_p(perm.data_ptr() if plan.nnz else 0),
+                                            _stream(stream)),
+           "spmttkrp_plan_permutation")
+    return perm
+
+
+def spmttkrp_plan_partition(plan: Plan, mode: int, off, stream=None) -> int:
+    """off: int64 CUDA tensor [kappa+1].  Returns kappa."""
+    kappa = ctypes.c_int(0)
+    _check(load().spmttkrp_plan_partition(plan.handle, int(mode),
+                                          ctypes.c_void_p(off.data_ptr()),
+                                          ctypes.byref(kappa), _stream(stream)),
+           "spmttkrp_plan_partition")
+    return int(kappa.value)
+
+
+def spmttkrp_plan_work_units(plan: Plan, mode: int, off, stream=None):
+    """off: int64 CUDA tensor [kappa*SPM_UNITS_PER_PARTITION(rank)+1]."""
+    _check(load().spmttkrp_plan_work_units(plan.handle, int(mode), ctypes.c_void_p(off.data_ptr()),
+                                           _stream(stream)),
+           "spmttkrp_plan_work_units")
+    return off
+
+
+def spmttkrp_plan_scheme(plan: Plan, mode: int) -> int:
+    out = ctypes.c_int(0)
+    _check(load().spmttkrp_plan_scheme(plan.handle, int(mode), ctypes.byref(out)),
+           "spmttkrp_plan_scheme")
+    return int(out.value)
+
+
+def spmttkrp_plan_destroy(plan: Plan):
+    plan.destroy()
+
+
+def spmttkrp_run(plan: Plan, mode: int, factors, out, stream=None):
+    """factors: N CUDA tensors (float32 or bfloat16 per the plan), I_w x R
+    row-major (factors[mode] may be None); out: float32 CUDA [I_mode, R]."""
+    _check(load().spmttkrp_run(plan.handle, int(mode), _ptrs(list(factors)),
+                               ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "spmttkrp_run")
+    return out
+
+
+def cpd_als_step(plan: Plan, factors, lam, fit=None, stream=None):
+    """One CP-ALS sweep; factors updated in place, lam float64 CUDA [R],
+    fit float64 CUDA [1] or None."""
+    _check(load().cpd_als_step(plan.handle, _ptrs(list(factors)),
+                               ctypes.c_void_p(lam.data_ptr()),
+                               ctypes.c_void_p(fit.data_ptr() if fit is not None else 0),
+                               _stream(stream)),
+           "cpd_als_step")
+
+
+def spmttkrp_plan_status(plan: Plan, stream=None) -> int:
+    """Synchronises and returns (and clears) the plan's device-side status."""
+    return int(load().spmttkrp_plan_status(plan.handle, _stream(stream)))

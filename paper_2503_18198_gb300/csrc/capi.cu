@@ -1,0 +1,204 @@
+// capi.cu -- the extern "C" entry points declared in include/spmttkrp.h.
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+#include <new>
+
+#include "plan.cuh"
+
+namespace spm {
+
+spm_status plan_alloc(spmttkrp_plan_s* p, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (p->nallocs >= (int)(sizeof(p->allocs) / sizeof(p->allocs[0]))) return SPM_ERR_OOM;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    *ptr = nullptr;
+    return e == cudaErrorMemoryAllocation ? SPM_ERR_OOM : SPM_ERR_CUDA;
+  }
+  p->allocs[p->nallocs++] = *ptr;
+  p->bytes += bytes;
+  return SPM_OK;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return -1;
+  }
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return -1;
+  }
+  return n;
+}
+
+namespace {
+
+void free_plan(spmttkrp_plan_s* p) {
+  if (!p) return;
+  for (int i = 0; i < p->nallocs; ++i) cudaFree(p->allocs[i]);
+  (void)cudaGetLastError();
+  delete p;
+}
+
+__global__ void perm_to_i64_kernel(const int32_t* __restrict__ in, int64_t n,
+                                   int64_t* __restrict__ out) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = in[k];
+}
+
+}  // namespace
+}  // namespace spm
+
+using namespace spm;
+
+extern "C" {
+
+const char* spm_status_string(spm_status s) {
+  switch (s) {
+    case SPM_OK: return "ok";
+    case SPM_ERR_INVALID_ARG: return "invalid argument";
+    case SPM_ERR_INDEX_OUT_OF_RANGE: return "index out of range";
+    case SPM_ERR_OOM: return "out of device memory";
+    case SPM_ERR_CUDA: return "CUDA runtime error";
+    case SPM_ERR_NUMERIC: return "numerical failure (system not positive definite or NaN)";
+    case SPM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SPM_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+int spm_device_sm_count(void) { return sm_count(); }
+
+spm_status spmttkrp_plan(spmttkrp_plan_t* out, int nmodes, const int64_t* dims, int64_t nnz,
+                         const int32_t* const* idx, const float* vals, int rank,
+                         uint32_t flags, void* stream) {
+  if (!out) return SPM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (nmodes < 2 || nmodes > SPM_MAX_MODES || !dims || nnz < 0 ||
+      nnz >= ((int64_t)1 << 31) - ((int64_t)1 << 20) || rank < 1 || rank > SPM_MAX_RANK)
+    return SPM_ERR_INVALID_ARG;
+  for (int w = 0; w < nmodes; ++w)
+    if (dims[w] < 1 || dims[w] >= ((int64_t)1 << 31)) return SPM_ERR_INVALID_ARG;
+  if (nnz > 0) {
+    if (!idx || !vals) return SPM_ERR_INVALID_ARG;
+    for (int w = 0; w < nmodes; ++w)
+      if (!idx[w]) return SPM_ERR_INVALID_ARG;
+  }
+  const uint32_t known = SPM_FACTOR_MASK | SPM_POLICY_MASK | (0xFFFFu << 16);
+  if (flags & ~known) return SPM_ERR_INVALID_ARG;
+  const int policy = (int)((flags & SPM_POLICY_MASK) >> 4);
+  if (policy > 3) return SPM_ERR_INVALID_ARG;
+  int kappa = (int)SPM_KAPPA_OF(flags);
+  if (kappa == 0) kappa = sm_count();
+  if (kappa < 1) return SPM_ERR_CUDA;
+
+  spmttkrp_plan_s* p = new (std::nothrow) spmttkrp_plan_s();
+  if (!p) return SPM_ERR_OOM;
+  cudaGetDevice(&p->device);
+  p->N = nmodes;
+  p->R = rank;
+  for (int w = 0; w < nmodes; ++w) p->dims[w] = dims[w];
+  p->nnz = nnz;
+  p->flags = flags;
+  p->bf16 = (flags & SPM_FACTOR_MASK) == SPM_FACTOR_BF16;
+  p->kappa = kappa;
+  p->nu = SPM_UNITS_PER_PARTITION(rank);
+  p->policy = policy;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  spm_status st = plan_alloc(p, (void**)&p->dev_err, sizeof(int));
+  if (st == SPM_OK) st = plan_alloc(p, (void**)&p->normX2, sizeof(double));
+  if (st == SPM_OK) st = plan_alloc(p, (void**)&p->cta_part, sizeof(float) * 2 * (size_t)kappa * rank);
+  if (st == SPM_OK) st = plan_alloc(p, (void**)&p->cta_meta, sizeof(int) * 4 * (size_t)kappa);
+  if (st == SPM_OK && cudaMemsetAsync(p->dev_err, 0, sizeof(int), s) != cudaSuccess) st = SPM_ERR_CUDA;
+  if (st == SPM_OK) st = build_copies(p, idx, vals, s);
+  if (st != SPM_OK) {
+    cudaStreamSynchronize(s);
+    (void)cudaGetLastError();
+    free_plan(p);
+    return st;
+  }
+  *out = p;
+  return SPM_OK;
+}
+
+spm_status spmttkrp_plan_bytes(spmttkrp_plan_t plan, size_t* bytes) {
+  if (!plan || !bytes) return SPM_ERR_INVALID_ARG;
+  *bytes = plan->bytes;
+  return SPM_OK;
+}
+
+spm_status spmttkrp_plan_permutation(spmttkrp_plan_t plan, int mode, int64_t* perm,
+                                     void* stream) {
+  if (!plan || mode < 0 || mode >= plan->N || (!perm && plan->nnz > 0)) return SPM_ERR_INVALID_ARG;
+  if (plan->nnz == 0) return SPM_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t n = plan->nnz;
+  const int blocks = (int)std::min<int64_t>(ceil_div<int64_t>(n, 256), 152 * 16);
+  perm_to_i64_kernel<<<blocks, 256, 0, s>>>(plan->mode[mode].perm, n, perm);
+  SPM_CUDA_TRY(cudaGetLastError());
+  return SPM_OK;
+}
+
+spm_status spmttkrp_plan_partition(spmttkrp_plan_t plan, int mode, int64_t* off, int* kappa_out,
+                                   void* stream) {
+  if (!plan || mode < 0 || mode >= plan->N || !off) return SPM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  SPM_CUDA_TRY(cudaMemcpyAsync(off, plan->mode[mode].off, sizeof(int64_t) * (plan->kappa + 1),
+                               cudaMemcpyDeviceToDevice, s));
+  if (kappa_out) *kappa_out = plan->kappa;
+  return SPM_OK;
+}
+
+spm_status spmttkrp_plan_work_units(spmttkrp_plan_t plan, int mode, int64_t* off, void* stream) {
+  if (!plan || mode < 0 || mode >= plan->N || !off) return SPM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  SPM_CUDA_TRY(cudaMemcpyAsync(off, plan->mode[mode].woff,
+                               sizeof(int64_t) * ((size_t)plan->kappa * plan->nu + 1),
+                               cudaMemcpyDeviceToDevice, s));
+  return SPM_OK;
+}
+
+spm_status spmttkrp_plan_scheme(spmttkrp_plan_t plan, int mode, int* scheme) {
+  if (!plan || mode < 0 || mode >= plan->N || !scheme) return SPM_ERR_INVALID_ARG;
+  *scheme = plan->mode[mode].scheme;
+  return SPM_OK;
+}
+
+void spmttkrp_plan_destroy(spmttkrp_plan_t plan) {
+  if (!plan) return;
+  cudaDeviceSynchronize();
+  free_plan(plan);
+}
+
+spm_status spmttkrp_run(spmttkrp_plan_t plan, int mode, const void* const* factors, float* out,
+                        void* stream) {
+  if (!plan) return SPM_ERR_INVALID_ARG;
+  return run_mttkrp(plan, mode, factors, out, static_cast<cudaStream_t>(stream));
+}
+
+spm_status cpd_als_step(spmttkrp_plan_t plan, void* const* factors, double* lambda, double* fit,
+                        void* stream) {
+  if (!plan || !factors || !lambda) return SPM_ERR_INVALID_ARG;
+  return als_sweep(plan, factors, lambda, fit, static_cast<cudaStream_t>(stream));
+}
+
+spm_status spmttkrp_plan_status(spmttkrp_plan_t plan, void* stream) {
+  if (!plan) return SPM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  SPM_CUDA_TRY(cudaMemcpyAsync(&h, plan->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SPM_CUDA_TRY(cudaStreamSynchronize(s));
+  SPM_CUDA_TRY(cudaMemsetAsync(plan->dev_err, 0, sizeof(int), s));
+  if (h & DEV_ERR_NUMERIC) return SPM_ERR_NUMERIC;
+  if (h & DEV_ERR_TIMEOUT) return SPM_ERR_TIMEOUT;
+  return SPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// mttkrp.cu -- launch sequence of one spMTTKRP along mode d (Algorithm 1's
+// body for one mode): [clear output if Scheme 1] -> mttkrp kernel over the
+// kappa partitions -> fix-up of rows that straddle partitions (Scheme 2).
+#include <algorithm>
+
+#include "mttkrp_kernel.cuh"
+
+namespace spm {
+
+using MttkrpKernelFn = void (*)(const MttkrpArgs);
+MttkrpKernelFn pick_mttkrp_f32_a(int nin, int R);
+MttkrpKernelFn pick_mttkrp_f32_b(int nin, int R);
+MttkrpKernelFn pick_mttkrp_bf16_a(int nin, int R);
+MttkrpKernelFn pick_mttkrp_bf16_b(int nin, int R);
+
+MttkrpKernelFn pick_mttkrp(bool bf16, int nin, int R) {
+  if (bf16) return nin <= 2 ? pick_mttkrp_bf16_a(nin, R) : pick_mttkrp_bf16_b(nin, R);
+  return nin <= 2 ? pick_mttkrp_f32_a(nin, R) : pick_mttkrp_f32_b(nin, R);
+}
+
+namespace {
+
+// Rows without nonzeros (bit clear in `mask`) are written as zeros.
+__global__ void zero_empty_rows_kernel(const uint32_t* __restrict__ mask, int64_t I, int R,
+                                       float* __restrict__ out) {
+  const int64_t n = I * R;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = x / R;
+    if (!((__ldg(&mask[row >> 5]) >> (row & 31)) & 1u)) out[x] = 0.f;
+  }
+}
+
+// One warp per partition z.  If z holds the start of a row that continues
+// into later partitions (its last-row partial), add the first-row partials
+// of the following partitions in partition order and store the row.
+__global__ void __launch_bounds__(256)
+    mttkrp_fixup_kernel(const float* __restrict__ cta_part, const int* __restrict__ cta_meta,
+                        int kappa, int R, float* __restrict__ out) {
+  const int z = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (z >= kappa) return;
+  const int* m = cta_meta + 4 * z;
+  if (!(m[2] & META_PART1)) return;
+  const int row = m[1];
+  float s[8];
+  const float* p1 = cta_part + (int64_t)(2 * z + 1) * R;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int r = lane + 32 * j;
+    s[j] = r < R ? p1[r] : 0.f;
+  }
+  for (int q = z + 1; q < kappa; ++q) {
+    const int* mq = cta_meta + 4 * q;
+    const int fq = mq[2];
+    if (fq & META_EMPTY) continue;
+    if (mq[0] != row) break;
+    const float* p0 = cta_part + (int64_t)(2 * q) * R;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int r = lane + 32 * j;
+      if (r < R) s[j] += p0[r];
+    }
+    if (!(mq[1] == row && (fq & META_SHARED_NEXT))) break;
+  }
+  float* dst = out + (int64_t)row * R;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int r = lane + 32 * j;
+    if (r < R) dst[r] = s[j];
+  }
+}
+
+}  // namespace
+
+spm_status run_mttkrp(spmttkrp_plan_s* p, int mode, const void* const* factors, float* out,
+                      cudaStream_t s) {
+  if (!p || mode < 0 || mode >= p->N || !factors || !out) return SPM_ERR_INVALID_ARG;
+  const int R = p->R;
+  const spm_mode_copy& c = p->mode[mode];
+  MttkrpArgs a{};
+  a.rec = c.rec;
+  a.woff = c.woff;
+  int m = 0;
+  for (int w = 0; w < p->N; ++w) {
+    if (w == mode) continue;
+    if (!factors[w] || (reinterpret_cast<uintptr_t>(factors[w]) & 15u)) return SPM_ERR_INVALID_ARG;
+    a.fac[m++] = factors[w];
+  }
+  if (reinterpret_cast<uintptr_t>(out) & 15u) return SPM_ERR_INVALID_ARG;
+  a.out = out;
+  a.cta_part = p->cta_part;
+  a.cta_meta = p->cta_meta;
+  a.nnz = p->nnz;
+  a.I = p->dims[mode];
+  a.R = R;
+  a.nin = p->N - 1;
+  a.nu = p->nu;
+  a.err = p->dev_err;
+  const size_t out_bytes = sizeof(float) * (size_t)a.I * (size_t)R;
+  if (p->nnz == 0) {
+    SPM_CUDA_TRY(cudaMemsetAsync(out, 0, out_bytes, s));
+    return SPM_OK;
+  }
+  if (c.scheme == 1) {
+    SPM_CUDA_TRY(cudaMemsetAsync(out, 0, out_bytes, s));
+  } else if (c.empty_rows > 0) {
+    const int64_t n4 = (int64_t)a.I * R;
+    const int blocks = (int)std::min<int64_t>(ceil_div<int64_t>(n4, 256), 152 * 16);
+    zero_empty_rows_kernel<<<blocks, 256, 0, s>>>(c.rowmask, a.I, R, out);
+    SPM_CUDA_TRY(cudaGetLastError());
+  }
+  MttkrpKernelFn fn = pick_mttkrp(p->bf16, p->N - 1, R);
+  const size_t smem = mttkrp_smem_bytes(R, record_int4s(p->N), p->nu);
+  SPM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // Smallest shared-memory carve-out that fits: the rest of the unified
+  // array is L1 for the gathered factor rows.
+  const int carve = (int)std::min<size_t>(100, (smem + 4096) * 100 / (228 * 1024) + 1);
+  SPM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+  fn<<<p->kappa, MT_THREADS, smem, s>>>(a);
+  SPM_CUDA_TRY(cudaGetLastError());
+  if (c.scheme != 1 && p->kappa > 1) {
+    const int threads = 256;
+    const int blocks = (int)ceil_div<int64_t>((int64_t)p->kappa * 32, threads);
+    mttkrp_fixup_kernel<<<blocks, threads, 0, s>>>(p->cta_part, p->cta_meta, p->kappa, R, out);
+    SPM_CUDA_TRY(cudaGetLastError());
+  }
+  return SPM_OK;
+}
+
+}  // namespace spm

@@ -1,0 +1,8 @@
+// FP32-factor MTTKRP instantiations, 4 modes and the generic >= 5 modes.
+#include "mttkrp_inst.cuh"
+
+namespace spm {
+MttkrpKernelFn pick_mttkrp_f32_b(int nin, int R) {
+  return nin == 3 ? pick_mttkrp_t<float, 3>(R) : pick_mttkrp_generic_t<float>(R);
+}
+}  // namespace spm

@@ -1,0 +1,39 @@
+// mttkrp_inst.cuh -- kernel selection for one factor storage type and a set
+// of input-mode counts.  Included by several translation units so that the
+// instantiations compile in parallel.
+#pragma once
+
+#include "mttkrp_kernel.cuh"
+
+namespace spm {
+
+using MttkrpKernelFn = void (*)(const MttkrpArgs);
+
+// Fast shapes: the rank is VEC * LPN * CPL with one 16-byte load per lane
+// and chunk.  Anything else uses the scalar variant (one nonzero per step).
+template <typename FT, int NIN>
+MttkrpKernelFn pick_mttkrp_t(int R) {
+  constexpr int RI = record_int4s(NIN > 0 ? NIN + 1 : SPM_MAX_MODES);
+  constexpr int VEC = 16 / (int)sizeof(FT);
+  if (R % VEC == 0) {
+    switch (R / VEC) {
+      case 1: return &mttkrp_kernel<RI, NIN, FT, VEC, 1, 1>;
+      case 2: return &mttkrp_kernel<RI, NIN, FT, VEC, 2, 1>;
+      case 4: return &mttkrp_kernel<RI, NIN, FT, VEC, 4, 1>;
+      case 8: return &mttkrp_kernel<RI, NIN, FT, VEC, 8, 1>;
+      case 16: return &mttkrp_kernel<RI, NIN, FT, VEC, 16, 1>;
+      case 32: return &mttkrp_kernel<RI, NIN, FT, VEC, 32, 1>;
+      case 64: return &mttkrp_kernel<RI, NIN, FT, VEC, 32, 2>;
+      default: break;
+    }
+  }
+  return &mttkrp_kernel<RI, NIN, FT, 1, 32, 8>;
+}
+
+// The generic-N variant (five or more modes) only has the scalar shape.
+template <typename FT>
+MttkrpKernelFn pick_mttkrp_generic_t(int) {
+  return &mttkrp_kernel<2, 0, FT, 1, 32, 8>;
+}
+
+}  // namespace spm

@@ -1,0 +1,518 @@
+// mttkrp_kernel.cuh -- the sm_103a spMTTKRP kernel for one output mode.
+//
+// What it computes (Eq. 1, Sec. II-A6, Algorithm 2): for the mode-d copy,
+//   M_d(c_d, r) = sum over nonzeros of val * prod_{w != d} Y_w(c_w, r).
+//
+// How (GB300 design, not the paper's block layout):
+//  * One thread block per partition B_{d,z} (Algorithm 1's parallel loop),
+//    1024 threads as in the paper's R x P = 32 x 32 block.  The partition is
+//    cut by the plan into NU contiguous work units; the block's 32 warps take
+//    units from a shared-memory counter, so a warp that drew cheap units
+//    takes more (dynamic balance inside the block, fixed merge order).
+//  * A warp streams its unit of the copy through a 3-stage ring of small
+//    shared-memory tiles filled by 1-D bulk copies (cp.async.bulk on the TMA
+//    engine, completion on an mbarrier).  Tiles are small so that most of
+//    the SM's unified L1/shared array stays L1 cache for factor rows.
+//  * A warp works on G consecutive nonzeros per step: each "slot" of LPN
+//    lanes takes one nonzero, each lane VEC ranks per 16-byte load, so a
+//    factor row is fetched as whole 128-byte lines.  U steps of records and
+//    gathers are issued before any of them is used, to keep loads in flight.
+//  * A tile whose first and last records are on the current output row lies
+//    entirely on it (rows are sorted), and is accumulated with no per-step
+//    row bookkeeping -- the common case on heavy rows.  Otherwise each step
+//    checks its rows with a warp vote; on a row change the slots' sums are
+//    combined with a segmented shuffle scan and finished rows are stored
+//    once.  Partial rows never round-trip through global memory (the paper's
+//    point about intermediate values, Sec. I).
+//  * Rows cut by a unit boundary are merged by the block with a segmented
+//    scan over the units' boundary partials in shared memory (the paper's
+//    Local_Update); rows cut by a partition boundary (equal-nnz or balanced
+//    policies) leave one partial per block in a small workspace that a fix-up
+//    kernel adds in partition order (the paper's Global_Update, made
+//    deterministic).
+//  * Rows with no nonzero are zeroed by a separate pass over a plan-time
+//    bitmap of non-empty rows.
+#pragma once
+
+#include "plan.cuh"
+
+namespace spm {
+
+constexpr int MT_WARPS = 32;
+constexpr int MT_THREADS = MT_WARPS * 32;
+#ifndef SPM_MT_STAGES
+#define SPM_MT_STAGES 3
+#endif
+#ifndef SPM_MT_TILE
+#define SPM_MT_TILE 64
+#endif
+constexpr int MT_STAGES = SPM_MT_STAGES;
+constexpr int MT_TILE_RECS = SPM_MT_TILE;  // records per stage tile (per warp)
+
+struct MttkrpArgs {
+  const int4* rec;        // copy records
+  const int64_t* woff;    // work-unit offsets [kappa * nu + 1]
+  const void* fac[SPM_MAX_MODES - 1];  // input factors in record order
+  float* out;             // I_d x R
+  float* cta_part;        // [kappa][2][R] boundary partials
+  int* cta_meta;          // [kappa][4] (first row, last row, flags, 0)
+  int* err;               // sticky device error flags
+  int64_t nnz;
+  int64_t I;              // rows of the output
+  int R;                  // rank (runtime; equals the template rank when exact)
+  int nin;                // number of input modes (N - 1)
+  int nu;                 // work units per partition
+};
+
+// cta_meta flags
+enum : int {
+  META_PART0 = 1,        // cta_part[z][0] holds the first row's partial
+  META_PART1 = 2,        // cta_part[z][1] holds the last row's partial
+  META_SHARED_PREV = 4,  // first row continues from the previous partition
+  META_SHARED_NEXT = 8,  // last row continues into the next partition
+  META_EMPTY = 16,
+};
+
+// Shared memory of one block: per-warp rings of record tiles and their
+// barriers, and two boundary partials (+ row ids) per work unit.
+inline size_t mttkrp_smem_bytes(int R, int RI, int nu) {
+  return (size_t)MT_WARPS * MT_STAGES * MT_TILE_RECS * 16 * RI +
+         (size_t)MT_WARPS * MT_STAGES * sizeof(uint64_t) + (size_t)2 * nu * R * sizeof(float) +
+         (size_t)2 * nu * sizeof(int);
+}
+
+// Raw 32-bit words of one lane's slice of a factor row, and their conversion.
+template <typename FT, int VEC>
+struct Slice;
+
+template <>
+struct Slice<float, 4> {
+  static constexpr int RAWN = 4;
+  static __device__ __forceinline__ void load(const void* base, int64_t row, int R, int r0,
+                                              uint32_t* raw) {
+    const uint4 x = __ldg(reinterpret_cast<const uint4*>(static_cast<const float*>(base) +
+                                                         row * R + r0));
+    raw[0] = x.x; raw[1] = x.y; raw[2] = x.z; raw[3] = x.w;
+  }
+  static __device__ __forceinline__ void cvt(const uint32_t* raw, float* f) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) f[i] = __uint_as_float(raw[i]);
+  }
+};
+
+template <>
+struct Slice<__nv_bfloat16, 8> {
+  static constexpr int RAWN = 4;
+  static __device__ __forceinline__ void load(const void* base, int64_t row, int R, int r0,
+                                              uint32_t* raw) {
+    const uint4 x = __ldg(reinterpret_cast<const uint4*>(
+        static_cast<const __nv_bfloat16*>(base) + row * R + r0));
+    raw[0] = x.x; raw[1] = x.y; raw[2] = x.z; raw[3] = x.w;
+  }
+  static __device__ __forceinline__ void cvt(const uint32_t* raw, float* f) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      f[2 * i] = __uint_as_float(raw[i] << 16);
+      f[2 * i + 1] = __uint_as_float(raw[i] & 0xFFFF0000u);
+    }
+  }
+};
+
+template <>
+struct Slice<float, 1> {
+  static constexpr int RAWN = 1;
+  static __device__ __forceinline__ void load(const void* base, int64_t row, int R, int r0,
+                                              uint32_t* raw) {
+    raw[0] = r0 < R ? __float_as_uint(__ldg(static_cast<const float*>(base) + row * R + r0)) : 0u;
+  }
+  static __device__ __forceinline__ void cvt(const uint32_t* raw, float* f) {
+    f[0] = __uint_as_float(raw[0]);
+  }
+};
+
+template <>
+struct Slice<__nv_bfloat16, 1> {
+  static constexpr int RAWN = 1;
+  static __device__ __forceinline__ void load(const void* base, int64_t row, int R, int r0,
+                                              uint32_t* raw) {
+    raw[0] = r0 < R ? (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(base) + row * R + r0)
+                    : 0u;
+  }
+  static __device__ __forceinline__ void cvt(const uint32_t* raw, float* f) {
+    f[0] = __uint_as_float(raw[0] << 16);
+  }
+};
+
+// Store one lane's VEC consecutive FP32 values (r0 .. r0+VEC-1) of a row.
+template <int VEC>
+__device__ __forceinline__ void store_vec(float* row_ptr, int R, int r0, const float* v) {
+  if constexpr (VEC % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < VEC / 4; ++q)
+      *reinterpret_cast<float4*>(row_ptr + r0 + 4 * q) =
+          make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e)
+      if (r0 + e < R) row_ptr[r0 + e] = v[e];
+  }
+}
+
+// NIN > 0: exactly NIN input modes.  NIN == 0: runtime a.nin (five or more
+// modes); the first two input modes are batched, further ones are fetched
+// when the step is computed.
+template <int RI, int NIN, typename FT, int VEC, int LPN, int CPL>
+__global__ void __launch_bounds__(MT_THREADS, 1) mttkrp_kernel(const MttkrpArgs a) {
+  using S = Slice<FT, VEC>;
+  constexpr int RAWN = S::RAWN;
+  constexpr int G = 32 / LPN;
+  constexpr int W = 4 * RI;
+  constexpr int NPIPE = NIN > 0 ? NIN : 2;  // batched input modes
+  constexpr int TILE = MT_TILE_RECS;
+  constexpr int tile_bytes = TILE * 16 * RI;
+  static_assert(TILE % G == 0, "tile geometry");
+  constexpr int PIPE_REGS = CPL * RAWN * NPIPE;
+#ifdef SPM_MT_BATCH
+  constexpr int U = NIN == 0 ? 1 : SPM_MT_BATCH;
+#else
+  constexpr int U = NIN == 0 ? 1 : (PIPE_REGS <= 4 ? 4 : (PIPE_REGS <= 8 ? 2 : 1));
+#endif
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int next_unit;
+
+  const int R = a.R;
+  const int NU = a.nu;
+  const int nin = NIN > 0 ? NIN : a.nin;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = lane / LPN, sub = lane % LPN;
+  const int z = blockIdx.x;
+  const int64_t* uoff = a.woff + (int64_t)z * NU;
+  const int64_t K0 = uoff[0], K1 = uoff[NU];
+
+  unsigned char* stages = smem + (size_t)warp * MT_STAGES * tile_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)MT_WARPS * MT_STAGES * tile_bytes) +
+                   warp * MT_STAGES;
+  float* part = reinterpret_cast<float*>(smem + (size_t)MT_WARPS * MT_STAGES * tile_bytes +
+                                         (size_t)MT_WARPS * MT_STAGES * sizeof(uint64_t));
+  int* prow = reinterpret_cast<int*>(part + (size_t)2 * NU * R);  // [2 * NU]
+
+  auto row_at = [&](int64_t k) -> int { return __ldg(&a.rec[k * RI].x); };
+  auto rank0 = [&](int c) -> int { return (c * LPN + sub) * VEC; };
+
+  if (lane == 0) {
+#pragma unroll
+    for (int st = 0; st < MT_STAGES; ++st) mbar_init(&bars[st], 1);
+    fence_mbar_init();
+  }
+  if (threadIdx.x == 0) next_unit = MT_WARPS;
+  __syncthreads();
+
+  int seq_issued = 0;    // ring sequence: tiles issued by this warp so far
+  bool timeout = false;
+
+  auto slot_reduce = [&](float (&x)[CPL][VEC]) {
+#pragma unroll
+    for (int o = LPN; o < 32; o <<= 1)
+#pragma unroll
+      for (int c = 0; c < CPL; ++c)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) x[c][e] += __shfl_xor_sync(SPM_FULL_MASK, x[c][e], o);
+  };
+
+  for (int u = warp; u < NU && !timeout;) {
+    const int64_t k0 = uoff[u], k1 = uoff[u + 1];
+    const int lenw = (int)(k1 - k0);
+    float* pf = part + (size_t)(2 * u) * R;
+    float* pl = pf + R;
+    if (lenw > 0) {
+      const int ntiles = (lenw + TILE - 1) / TILE;
+      const int seq0 = seq_issued;  // ring sequence number of this unit's tile 0
+      auto issue = [&](int t) {     // lane 0 only
+        const int64_t kb = k0 + (int64_t)t * TILE;
+        const int64_t cnt = (k1 - kb) < TILE ? (k1 - kb) : TILE;
+        const uint32_t bytes = (uint32_t)(cnt * 16 * RI);
+        const int q = seq0 + t;
+        uint64_t* bar = &bars[q % MT_STAGES];
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(stages + (q % MT_STAGES) * tile_bytes, a.rec + kb * RI, bytes, bar);
+      };
+      int issued = ntiles < MT_STAGES ? ntiles : MT_STAGES;
+      if (lane == 0)
+        for (int t = 0; t < issued; ++t) issue(t);
+
+      const int first_row = row_at(k0);
+      int cur = first_row;
+      float acc[CPL][VEC];
+#pragma unroll
+      for (int c = 0; c < CPL; ++c)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[c][e] = 0.f;
+
+      // finished row from this slot's lanes; the unit's first row goes to the
+      // block's boundary partials
+      auto put_row = [&](int row, const float (&x)[CPL][VEC]) {
+        float* dst = row == first_row ? pf : a.out + (int64_t)row * R;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) store_vec<VEC>(dst, R, rank0(c), x[c]);
+      };
+
+      // Fold one step's contributions v (rows `row`, empty slots already on
+      // the last row) into the running row state.
+      auto step_rows = [&](int row, float (&v)[CPL][VEC]) {
+        if (__all_sync(SPM_FULL_MASK, row == cur)) {
+#pragma unroll
+          for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) acc[c][e] += v[c][e];
+          return;
+        }
+        // Row change inside this step: carry = total of `cur` so far.
+        slot_reduce(acc);
+        const int next_row = __shfl_down_sync(SPM_FULL_MASK, row, LPN);
+        const bool tail = (slot == G - 1) || next_row != row;
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {  // segmented inclusive scan over slots
+          const int ru = __shfl_up_sync(SPM_FULL_MASK, row, o * LPN);
+#pragma unroll
+          for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+              const float t = __shfl_up_sync(SPM_FULL_MASK, v[c][e], o * LPN);
+              if (slot >= o && ru == row) v[c][e] += t;
+            }
+        }
+        if (row == cur) {
+#pragma unroll
+          for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) v[c][e] += acc[c][e];
+        }
+        const int row0 = __shfl_sync(SPM_FULL_MASK, row, 0);
+        const int rowl = __shfl_sync(SPM_FULL_MASK, row, 31);
+        if (row0 != cur && slot == 0) put_row(cur, acc);  // cur ended with the last step
+        if (tail && row != rowl) put_row(row, v);
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) acc[c][e] = (slot == G - 1) ? v[c][e] : 0.f;
+        cur = rowl;
+      };
+
+      for (int t = 0; t < ntiles; ++t) {
+        if (t > 0) {
+          __syncwarp();  // every lane is done with tile t-1: refill its stage
+          if (issued < ntiles) {
+            if (lane == 0) {
+              fence_proxy_async_smem();
+              issue(issued);
+            }
+            ++issued;
+          }
+        }
+        {
+          const int q = seq0 + t;
+          const bool ok = mbar_wait_bounded(&bars[q % MT_STAGES], (uint32_t)((q / MT_STAGES) & 1));
+          timeout = __any_sync(SPM_FULL_MASK, !ok);
+        }
+        if (timeout) {
+          // let every copy this warp started land before giving up
+          for (int q = seq0 + t + 1; q < seq0 + issued; ++q)
+            (void)mbar_wait_bounded(&bars[q % MT_STAGES], (uint32_t)((q / MT_STAGES) & 1), 1u << 20);
+          if (lane == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
+          break;
+        }
+        const int4* recs =
+            reinterpret_cast<const int4*>(stages + ((seq0 + t) % MT_STAGES) * tile_bytes);
+        const int n = (lenw - t * TILE) < TILE ? (lenw - t * TILE) : TILE;
+        const int nst = (n + G - 1) / G;
+        const bool pure = recs[0].x == cur && recs[(n - 1) * RI].x == cur;
+        for (int j = 0; j < nst; j += U) {
+          int w[U][W];
+          bool valid[U];
+          uint32_t y[U][NPIPE][CPL][RAWN];
+#pragma unroll
+          for (int uu = 0; uu < U; ++uu) {
+            const int pos = (j + uu) * G + slot;
+            valid[uu] = (j + uu) < nst && pos < n;
+#pragma unroll
+            for (int qq = 0; qq < W; ++qq) w[uu][qq] = 0;
+            if (valid[uu]) {
+#pragma unroll
+              for (int qq = 0; qq < RI; ++qq) {
+                const int4 v4 = recs[pos * RI + qq];
+                w[uu][4 * qq] = v4.x; w[uu][4 * qq + 1] = v4.y;
+                w[uu][4 * qq + 2] = v4.z; w[uu][4 * qq + 3] = v4.w;
+              }
+            }
+          }
+#pragma unroll
+          for (int uu = 0; uu < U; ++uu)
+#pragma unroll
+            for (int m = 0; m < NPIPE; ++m) {
+#pragma unroll
+              for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int i = 0; i < RAWN; ++i) y[uu][m][c][i] = 0u;
+              if (valid[uu] && m < nin) {
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) S::load(a.fac[m], w[uu][1 + m], R, rank0(c), y[uu][m][c]);
+              }
+            }
+#pragma unroll
+          for (int uu = 0; uu < U; ++uu) {
+            if (j + uu >= nst) break;
+            float v[CPL][VEC];
+            float val = 0.f;
+            if (NIN > 0) {
+              val = __int_as_float(w[uu][NIN > 0 ? NIN + 1 : 1]);
+            } else {
+#pragma unroll
+              for (int qq = 1; qq < W; ++qq)
+                if (qq == nin + 1) val = __int_as_float(w[uu][qq]);
+            }
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+              float f[VEC];
+              S::cvt(y[uu][0][c], f);
+#pragma unroll
+              for (int e = 0; e < VEC; ++e) v[c][e] = val * f[e];
+#pragma unroll
+              for (int m = 1; m < NPIPE; ++m)
+                if (m < nin) {
+                  S::cvt(y[uu][m][c], f);
+#pragma unroll
+                  for (int e = 0; e < VEC; ++e) v[c][e] *= f[e];
+                }
+              if (NIN == 0) {
+                for (int m = NPIPE; m < nin; ++m) {
+                  int idx = 0;
+#pragma unroll
+                  for (int qq = 1; qq < W; ++qq)
+                    if (qq == 1 + m) idx = w[uu][qq];
+                  uint32_t raw[RAWN];
+                  if (valid[uu]) S::load(a.fac[m], idx, R, rank0(c), raw);
+                  else raw[0] = 0u;
+                  S::cvt(raw, f);
+#pragma unroll
+                  for (int e = 0; e < VEC; ++e) v[c][e] *= f[e];
+                }
+              }
+            }
+            if (pure) {
+#pragma unroll
+              for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) acc[c][e] += v[c][e];
+            } else {
+              int row = w[uu][0];
+              if ((j + uu + 1) * G > n) {  // ragged step: empty slots join the last row
+                const int nvalid = n - (j + uu) * G;
+                const int lastv = __shfl_sync(SPM_FULL_MASK, row, (nvalid - 1) * LPN);
+                if (!valid[uu]) row = lastv;
+              }
+              step_rows(row, v);
+            }
+          }
+        }
+      }
+      // the unit's last row (== cur): its partial goes to the block merge
+      slot_reduce(acc);
+      const bool distinct_last = cur != first_row;
+      if (slot == 0) {
+        float* dst = distinct_last ? pl : pf;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) store_vec<VEC>(dst, R, rank0(c), acc[c]);
+      }
+      if (!distinct_last)
+        for (int r = lane; r < R; r += 32) pl[r] = 0.f;
+      if (lane == 0) {
+        prow[2 * u] = first_row;
+        prow[2 * u + 1] = distinct_last ? cur : -1;
+      }
+      seq_issued = seq0 + ntiles;
+    } else {
+      for (int r = lane; r < 2 * R; r += 32) pf[r] = 0.f;
+      if (lane == 0) {
+        prow[2 * u] = -1;
+        prow[2 * u + 1] = -1;
+      }
+    }
+    int nu_next = 0;
+    if (lane == 0) nu_next = atomicAdd(&next_unit, 1);
+    u = __shfl_sync(SPM_FULL_MASK, nu_next, 0);
+  }
+  __syncthreads();
+
+  // ---- block merge of the unit-boundary partials ---------------------------
+  // Entries e = 2u (first row of unit u) and 2u+1 (its distinct last row) in
+  // copy order.  Missing entries take the row of the entry before them with a
+  // zero value, so rows stay sorted and every run of equal rows is one group.
+  // An inclusive segmented scan (Hillis-Steele, fixed order) leaves each
+  // group's total on its last entry.
+  int* meta = a.cta_meta + 4 * z;
+  const int64_t len = K1 - K0;
+  if (len == 0) {
+    if (threadIdx.x == 0) { meta[0] = -1; meta[1] = -1; meta[2] = META_EMPTY; meta[3] = 0; }
+    return;
+  }
+  const int NE = 2 * NU;  // <= 256
+  // rows of missing entries (value already zero): running maximum of the
+  // entries so far, i.e. the row of the last real entry (-1 before any)
+  if (warp == 0) {
+    int m = -1;
+    const int per = (NE + 31) / 32;
+    const int e0 = lane * per;
+    for (int e = e0; e < e0 + per && e < NE; ++e) m = max(m, prow[e]);
+    int incl = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(SPM_FULL_MASK, incl, o);
+      if (lane >= o) incl = max(incl, t);
+    }
+    int run = __shfl_up_sync(SPM_FULL_MASK, incl, 1);
+    if (lane == 0) run = -1;
+    for (int e = e0; e < e0 + per && e < NE; ++e) {
+      run = max(run, prow[e]);
+      prow[e] = run;
+    }
+  }
+  __syncthreads();
+  // inclusive segmented scan of the partials, rows as segment keys
+  for (int d = 1; d < NE; d <<= 1) {
+    float tmp[8];
+    int cnt = 0;
+    for (int x = threadIdx.x; x < NE * R; x += MT_THREADS, ++cnt) {
+      const int e = x / R;
+      tmp[cnt] = (e >= d && prow[e - d] == prow[e]) ? part[x - d * R] : 0.f;
+    }
+    __syncthreads();
+    cnt = 0;
+    for (int x = threadIdx.x; x < NE * R; x += MT_THREADS, ++cnt) part[x] += tmp[cnt];
+    __syncthreads();
+  }
+  // each group's last entry holds the group total
+  const int F = row_at(K0);
+  const int L = row_at(K1 - 1);
+  const bool shared_prev = K0 > 0 && row_at(K0 - 1) == F;
+  const bool shared_next = K1 < a.nnz && row_at(K1) == L;
+  float* part0 = a.cta_part + (int64_t)(2 * z) * R;
+  float* part1 = part0 + R;
+  for (int x = threadIdx.x; x < NE * R; x += MT_THREADS) {
+    const int e = x / R, r = x % R;
+    const int row = prow[e];
+    if (row < 0 || (e + 1 < NE && prow[e + 1] == row)) continue;
+    float* dst;
+    if (row == F && shared_prev) dst = part0;
+    else if (row == L && shared_next) dst = part1;
+    else dst = a.out + (int64_t)row * R;
+    dst[r] = part[x];
+  }
+  if (threadIdx.x == 0) {
+    int flags = (shared_prev ? META_SHARED_PREV : 0) | (shared_next ? META_SHARED_NEXT : 0);
+    if (shared_prev) flags |= META_PART0;
+    if (shared_next && !(F == L && shared_prev)) flags |= META_PART1;
+    meta[0] = F; meta[1] = L; meta[2] = flags; meta[3] = 0;
+  }
+}
+
+}  // namespace spm

@@ -1,0 +1,77 @@
+// plan.cuh -- the plan object and the internal entry points between the
+// library's translation units.
+#pragma once
+
+#include "common.cuh"
+
+struct spm_mode_copy {
+  int4* rec = nullptr;       // records, record_int4s(N) int4 per nonzero
+  int32_t* perm = nullptr;   // input position of each copy position
+  int64_t* off = nullptr;    // device int64[kappa+1] partition offsets
+  int64_t* woff = nullptr;   // device int64[kappa*nu+1] work-unit offsets
+  uint32_t* rowmask = nullptr;  // bit i set: output row i has a nonzero
+  int64_t empty_rows = 0;    // rows without nonzeros
+  int scheme = 0;            // 0 cost-balanced, 1 or 2 (Sec. III-B)
+};
+
+struct spm_als_state {
+  bool ready = false;                 // Gram cache valid for `fac_ptr`
+  const void* fac_ptr[SPM_MAX_MODES] = {};
+  double* gram = nullptr;             // [N][R*R] Grams of the stored factors
+  double* gram_part = nullptr;        // [gram_blocks][R*R] block partials
+  int gram_blocks = 0;
+  double* chol = nullptr;             // R*R: Cholesky factor of V (lower)
+  float* winv = nullptr;              // 2*R*R: V^{-1} as hi/lo float pairs
+  double* colsq_part = nullptr;       // [gram_blocks][R] column sums of Z^2
+  double* inner_part = nullptr;       // [gram_blocks][R] sums of M .* Y
+  double* lambda_ws = nullptr;        // R
+  float* M = nullptr;                 // Imax*R MTTKRP output
+  float* Z = nullptr;                 // Imax*R unnormalised update
+};
+
+struct spmttkrp_plan_s {
+  int device = 0;
+  int N = 0;
+  int R = 0;
+  int64_t dims[SPM_MAX_MODES] = {};
+  int64_t nnz = 0;
+  uint32_t flags = 0;
+  bool bf16 = false;
+  int kappa = 0;
+  int nu = 0;      // work units per partition
+  int policy = 0;  // SPM_POLICY_* >> 4
+  spm_mode_copy mode[SPM_MAX_MODES];
+  // MTTKRP workspace: per-partition boundary-row partial sums.
+  float* cta_part = nullptr;   // [kappa][2][R]
+  int* cta_meta = nullptr;     // [kappa][4]
+  // Device scalars.
+  int* dev_err = nullptr;      // sticky error flags (spm::DEV_ERR_*)
+  double* normX2 = nullptr;    // |X|_F^2 (duplicates summed)
+  double* norm_part = nullptr; // partials for normX2
+  spm_als_state als;
+  size_t bytes = 0;
+  // allocation bookkeeping
+  void* allocs[64] = {};
+  int nallocs = 0;
+};
+
+namespace spm {
+
+// Allocation owned by the plan (recorded for destroy and for plan_bytes).
+spm_status plan_alloc(spmttkrp_plan_s* p, void** ptr, size_t bytes);
+
+// P1 + P2: build every mode copy and its partition (plan.cu).
+spm_status build_copies(spmttkrp_plan_s* p, const int32_t* const* idx,
+                        const float* vals, cudaStream_t s);
+
+// P3 + P4: one MTTKRP launch sequence for mode d (mttkrp.cu).
+spm_status run_mttkrp(spmttkrp_plan_s* p, int mode, const void* const* factors,
+                      float* out, cudaStream_t s);
+
+// P6: one CP-ALS sweep (als.cu).
+spm_status als_sweep(spmttkrp_plan_s* p, void* const* factors, double* lambda,
+                     double* fit, cudaStream_t s);
+
+int sm_count();
+
+}  // namespace spm

@@ -246,6 +246,37 @@ def test_partition_equal(nnz, kappa):
     assert all(off[z] == (z * nnz) // kappa for z in range(kappa + 1))
 
 
+@pytest.mark.parametrize("parts,row_cost", [(1, 4), (7, 4), (64, 4), (13, 0), (300, 9)])
+def test_partition_balanced_defining_property(parts, row_cost):
+    """Each boundary is the first position whose prefix cost reaches its share
+    (checked directly from per-nonzero costs, not through the oracle's prefix
+    sweep), boundaries are monotone, and every unit's cost is within one
+    nonzero's cost of the ideal share."""
+    dims, idx, vals = synth.coo_distinct((400, 90, 30), 5000, (1.2, 1.0, None), seed=parts)
+    for d in range(3):
+        off = oracle.partition_balanced(idx, d, parts, row_cost)
+        rows = idx[d][oracle.mode_permutation(idx, d)]
+        cost = np.ones(rows.size, dtype=np.int64)
+        cost[0] += row_cost
+        cost[1:] += row_cost * (rows[1:] != rows[:-1])
+        C = np.concatenate([[0], np.cumsum(cost)])
+        total = C[-1]
+        assert off[0] == 0 and off[-1] == rows.size and np.all(np.diff(off) >= 0)
+        for j in range(parts + 1):
+            k = off[j]
+            assert C[k] * parts >= j * total
+            assert k == 0 or C[k - 1] * parts < j * total
+        unit_cost = C[off[1:]] - C[off[:-1]]
+        assert unit_cost.max() <= total / parts + 1 + row_cost
+
+
+def test_partition_balanced_zero_row_cost_is_equal_split():
+    dims, idx, vals = synth.coo_random((50, 40, 30), 997, seed=3, duplicates=True)
+    for parts in (1, 5, 64, 2000):
+        off = oracle.partition_balanced(idx, 1, parts, row_cost=0)
+        assert np.array_equal(off, [-((-j * 997) // parts) for j in range(parts + 1)])
+
+
 @pytest.mark.parametrize("kappa", [1, 3, 5, 40])
 def test_partition_scheme1_bruteforce(kappa):
     dims, idx, vals = synth.coo_random((23, 7, 6), 200, seed=kappa, duplicates=True)
