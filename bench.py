@@ -1,0 +1,394 @@
+"""Benchmark: spMTTKRP along every mode of the 50M-nonzero 3-mode workload.
+
+Workload (synthetic stand-in for the paper's FROSTT tensors): 3-mode COO
+tensor 1,000,000 x 500,000 x 200,000, coordinates per mode truncated
+Zipf(1.2) with repeated cells removed, 50M nonzeros, values U(0,1), int32
+indices, R = 32 FP32 factors N(0,1).  One mode-specific copy per mode is
+resident in HBM (the plan, built before timing, as the workload states).
+
+A step is spMTTKRP along modes 0, 1, 2 (output clearing, the MTTKRP kernel,
+the partition fix-up; Algorithm 1 over all modes).  The plan build (copy
+sorting and partitioning) and one CP-ALS sweep are timed separately and
+reported beside the step.
+
+Metric: spMTTKRP HBM GB/s over all modes, B_d / t_d summed over modes with
+B_d = nnz*(4N+4) + sum_{w != d} U_w*R*4 + I_d*R*4 (streamed records, each
+distinct gathered factor row once, the output written once).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (the method does not
+shard; see the design notes) and rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spMTTKRP HBM GB/s & roofline %, all modes; CPD solves/s + p50/p99 latency"
+UNIT = "GB/s"
+WORKLOAD = "scale: 3-mode COO 1,000,000x500,000x200,000, 50M nnz, Zipf(1.2) coordinates " \
+           "deduplicated, U(0,1) values, R=32 FP32 factors, MTTKRP along all 3 modes"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nnz", type=int, default=50_000_000,
+                    help="nonzeros (the workload is 50M; smaller only for quick checks)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def algorithmic_bytes(dims, nnz, R, distinct, s_f=4):
+    """B_d per mode: records + distinct gathered rows + output rows."""
+    N = len(dims)
+    out = []
+    for d in range(N):
+        b = nnz * (4 * N + 4)
+        b += sum(distinct[w] * R * s_f for w in range(N) if w != d)
+        b += dims[d] * R * 4
+        out.append(b)
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def host_sample(dims, idx, vals, Y, sample_nnz):
+    import numpy as np
+    n = int(sample_nnz)
+    h_idx = [c[:n].cpu().numpy() for c in idx]
+    h_vals = vals[:n].cpu().numpy()
+    h_Y = [y.cpu().numpy().astype(np.float64) for y in Y]
+    return h_idx, h_vals, h_Y
+
+
+def time_oracle(dims, h_idx, h_vals, h_Y, R):
+    """One pass of the oracle MTTKRP over all modes; returns (seconds, bytes)."""
+    import numpy as np
+    import oracle
+    n = h_vals.size
+    distinct = [int(np.unique(c).size) for c in h_idx]
+    t0 = time.perf_counter()
+    for d in range(len(dims)):
+        oracle.mttkrp(dims, h_idx, h_vals, h_Y, d)
+    dt = time.perf_counter() - t0
+    return dt, sum(algorithmic_bytes(dims, n, R, distinct))
+
+
+def cpu_baseline(dims, idx, vals, Y, R, target_s):
+    """The oracle as it stands, single-threaded, on a prefix sample of the
+    workload's nonzeros (the same tensor's first nonzeros in draw order)."""
+    probe = 1_000_000
+    h = host_sample(dims, idx, vals, Y, probe)
+    dt, _ = time_oracle(dims, *h, R)
+    n = int(min(vals.numel(), max(probe, probe * target_s / max(dt, 1e-3))))
+    h = host_sample(dims, idx, vals, Y, n)
+    dt, b = time_oracle(dims, *h, R)
+    return {"value": b / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} of the workload's nonzeros (draw order), all 3 modes, "
+                      f"{dt:.1f} s single-threaded FP64"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores, same metric/unit."""
+    if rank != 0:
+        return
+    import synth
+    import torch
+    torch.set_num_threads(max(1, os.cpu_count() or 1))
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    dims, idx, vals, R, Y = synth.preset_torch("scale", nnz=args.nnz, device=dev)
+    n = min(args.nnz, 2_000_000)
+    h = host_sample(dims, idx, vals, Y, n)
+    for _ in range(args.warmup):
+        time_oracle(dims, *h, R)
+    tot_s, tot_b = 0.0, 0
+    for _ in range(args.steps):
+        dt, b = time_oracle(dims, *h, R)
+        tot_s += dt
+        tot_b += b
+    v = tot_b / tot_s / 1e9
+    sample = f"first {n} of the workload's nonzeros per step, all 3 modes, single-threaded FP64 oracle"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_nnz": n},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+        flush=True)
+
+
+def main():
+    args = parse()
+    import torch
+    rank, world, local = dist_init(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import synth
+    import paper_2503_18198_gb300 as spm
+    spm.load()  # fails loudly if the CUDA library is missing
+
+    dims, idx, vals, R, Y = synth.preset_torch("scale", nnz=args.nnz, device="cuda")
+    N = len(dims)
+    nnz = int(vals.numel())
+    distinct = [int((torch.bincount(c.long(), minlength=dims[w]) > 0).sum())
+                for w, c in enumerate(idx)]
+    B = algorithmic_bytes(dims, nnz, R, distinct)
+    stream = torch.cuda.current_stream()
+
+    # P1 + P2: plan build (timed once, not part of the step)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = spm.spmttkrp_plan(dims, idx, vals, R)
+    torch.cuda.synchronize()
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    outs = [torch.empty(dims[d], R, device="cuda") for d in range(N)]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(evs=None):
+        for d in range(N):
+            if evs is not None:
+                evs[d][0].record(stream)
+            spm.spmttkrp_run(plan, d, Y, outs[d])
+            if evs is not None:
+                evs[d][1].record(stream)
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    per_mode = [0.0] * N
+    for _ in range(args.steps):
+        flush.zero_()  # evict L2 between steps (outside the events)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(N)]
+        step(evs)
+        torch.cuda.synchronize()
+        for d in range(N):
+            per_mode[d] += evs[d][0].elapsed_time(evs[d][1])
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    step_ms = sum(per_mode) / args.steps
+    step_ms = max_over_ranks(step_ms, world)
+    mode_ms = [m / args.steps for m in per_mode]
+    value = world * sum(B) / (step_ms * 1e-3) / 1e9
+
+    # roofline of the MTTKRP launches (the dominant kernel)
+    peak, peak_kind = measured_peak()
+    achieved = sum(B) / (sum(mode_ms) * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "mttkrp_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            with open(tfile) as f:
+                tj = json.load(f)
+            if tj.get("nnz") == nnz:
+                traffic = tj.get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+
+    # e2e through the C ABI with host buffers: factors in from pinned host
+    # memory, MTTKRP along all modes, outputs back to host, every step.
+    hY = [y.cpu().pin_memory() for y in Y]
+    hout = [torch.empty(dims[d], R).pin_memory() for d in range(N)]
+    dY = [torch.empty_like(y) for y in Y]
+    h2d = sum(y.numel() * 4 for y in hY)
+    d2h = sum(o.numel() * 4 for o in hout)
+
+    def e2e_step():
+        for w in range(N):
+            dY[w].copy_(hY[w], non_blocking=True)
+        for d in range(N):
+            spm.spmttkrp_run(plan, d, dY, outs[d])
+            hout[d].copy_(outs[d], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(3, min(args.steps, 10))
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world)
+    e2e_value = world * sum(B) / (e2e_ms * 1e-3) / 1e9
+
+    # one CP-ALS sweep (P6 included) on the same plan, beside the step
+    lam = torch.empty(R, dtype=torch.float64, device="cuda")
+    fit = torch.empty(1, dtype=torch.float64, device="cuda")
+    fac = [y.clone() for y in Y]
+    spm.cpd_als_step(plan, fac, lam, fit)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    spm.cpd_als_step(plan, fac, lam, fit)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    als_ms = a0.elapsed_time(a1)
+
+    launches_per_step = sum(1 + (1 if plan_kappa(spm, plan) > 1 else 0) +
+                            (1 if distinct[d] < dims[d] else 0) for d in range(N))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(dims, idx, vals, Y, R, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nnz": nnz, "dims": list(dims), "rank": R,
+                       "factor_dtype": "fp32", "policy": "balanced",
+                       "step": "spMTTKRP along modes 0,1,2 on resident mode copies",
+                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "per_mode_ms": [round(m, 4) for m in mode_ms],
+            "per_mode_roofline_frac": [round(b / (m * 1e-3) / 1e9 / peak, 4)
+                                       for b, m in zip(B, mode_ms)],
+            "nnz_per_s_per_mode": [round(nnz / (m * 1e-3), 1) for m in mode_ms],
+            "effective_gather_GBs": round(nnz * (N - 1) * R * 4 * N / (sum(mode_ms) * 1e-3) / 1e9, 1),
+            "algorithmic_bytes_per_mode": B,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "mttkrp_kernel (+ row zero-fill and partition fix-up of the same call)",
+                         "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "plan_ms": plan_ms,
+            "als_sweep_ms": als_ms,
+            "plan_bytes": spm.spmttkrp_plan_bytes(plan),
+        }
+        print(json.dumps(line), flush=True)
+    plan.destroy()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def plan_kappa(spm, plan):
+    import torch
+    off = torch.empty(65536 + 1, dtype=torch.int64, device="cuda")
+    return spm.spmttkrp_plan_partition(plan, 0, off)
+
+
+if __name__ == "__main__":
+    main()
