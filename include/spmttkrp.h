@@ -188,6 +188,39 @@ void spmttkrp_plan_destroy(spmttkrp_plan_t plan);
 spm_status spmttkrp_run(spmttkrp_plan_t plan, int mode,
                         const void *const *factors, float *out, void *stream);
 
+/* MTTKRP along one mode with no device allocation (the paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * while they run, e.g. a serving loop confined to a memory pool sized at
+ * start-up, or code running where cudaMalloc would synchronise the device).
+ *
+ * The caller passes a mode copy it holds itself instead of a plan:
+ *  nmodes, dims, rank  as for spmttkrp_plan; mode = the output mode d.
+ *  records  device, nnz records of 16 * ceil((nmodes+1)/4) bytes each:
+ *           int32 words [c_d, c_w for w != d in ascending w, value bits
+ *           (FP32), zero padding], sorted by c_d (records of one output row
+ *           contiguous, rows ascending).  16-byte aligned.
+ *  factors  host array of nmodes device pointers as for spmttkrp_run.
+ *  flags    SPM_FACTOR_* and SPM_KAPPA(k); work units are equal nonzero
+ *           splits (no plan, so no cost-balanced partition).
+ *  out      device float[dims[mode] * rank], overwritten.
+ * Its only scratch (work-unit offsets and partition boundary partials) is a
+ * file-scope __device__ array of SPM_NOALLOC_SCRATCH_BYTES that every GPU
+ * holds from library load to process exit; a request whose scratch would
+ * exceed it (roughly kappa * (8*rank + 16) + 8 * kappa * units bytes)
+ * returns SPM_ERR_UNSUPPORTED.  The call allocates nothing (no cudaMalloc,
+ * no cudaFree, no allocating library routine); it clears `out` with
+ * cudaMemsetAsync and writes every scratch byte it later reads, so nothing
+ * carries over from the previous call.  All calls share the one array:
+ * calls that overlap on the GPU (different streams without ordering, or
+ * different host threads) race and give wrong results.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. */
+#define SPM_NOALLOC_SCRATCH_BYTES (1u << 20)
+spm_status spmttkrp_run_noalloc(int nmodes, const int64_t *dims, int64_t nnz,
+                                int mode, int rank, const void *records,
+                                const void *const *factors, uint32_t flags,
+                                float *out, void *stream);
+
 /* ---- CPD-ALS --------------------------------------------------------------- */
 
 /* One CP-ALS sweep over modes 0..N-1 in order (Sec. II-A5), Gauss-Seidel:

@@ -49,7 +49,8 @@ _lib = None
 SYMBOLS = ("spmttkrp_plan", "spmttkrp_plan_bytes", "spmttkrp_plan_permutation",
            "spmttkrp_plan_partition", "spmttkrp_plan_work_units", "spmttkrp_plan_scheme",
            "spmttkrp_plan_destroy", "spmttkrp_run", "cpd_als_step",
-           "spmttkrp_plan_status", "spm_status_string", "spm_device_sm_count")
+           "spmttkrp_plan_status", "spm_status_string", "spm_device_sm_count",
+           "spmttkrp_run_noalloc")
 
 
 def library_path() -> str:
@@ -93,6 +94,8 @@ def load(build_if_missing: bool = False):
     lib.spmttkrp_plan_status.restype = i32
     lib.spm_status_string.argtypes = [i32]
     lib.spm_status_string.restype = ctypes.c_char_p
+    lib.spmttkrp_run_noalloc.argtypes = [i32, P, i64, i32, i32, P, P, u32, P, P]
+    lib.spmttkrp_run_noalloc.restype = i32
     lib.spm_device_sm_count.argtypes = []
     lib.spm_device_sm_count.restype = i32
     _lib = lib
@@ -233,3 +236,19 @@ def cpd_als_step(plan: Plan, factors, lam, fit=None, stream=None):
 def spmttkrp_plan_status(plan: Plan, stream=None) -> int:
     """Synchronises and returns (and clears) the plan's device-side status."""
     return int(load().spmttkrp_plan_status(plan.handle, _stream(stream)))
+
+
+def spmttkrp_run_noalloc(dims, mode: int, rank: int, records, factors, out, flags: int = 0,
+                         stream=None):
+    """No-allocation MTTKRP from a caller-held mode copy.  records: int32
+    CUDA tensor [nnz, 4*ceil((N+1)/4)] in the documented record layout,
+    sorted by the output-mode index; factors/out as for spmttkrp_run."""
+    N = len(dims)
+    dims_a = (ctypes.c_int64 * N)(*[int(d) for d in dims])
+    nnz = int(records.shape[0]) if records is not None else 0
+    _check(load().spmttkrp_run_noalloc(N, dims_a, nnz, int(mode), int(rank),
+                                       ctypes.c_void_p(records.data_ptr() if nnz else 0),
+                                       _ptrs(list(factors)), int(flags) & 0xFFFFFFFF,
+                                       ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "spmttkrp_run_noalloc")
+    return out

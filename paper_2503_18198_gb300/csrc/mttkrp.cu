@@ -73,6 +73,18 @@ __global__ void __launch_bounds__(256)
 
 }  // namespace
 
+// Launch the partition fix-up on given boundary partials (used by callers
+// that keep those partials outside a plan).
+spm_status launch_mttkrp_fixup(const float* cta_part, const int* cta_meta, int kappa, int R,
+                               float* out, cudaStream_t s) {
+  if (kappa <= 1) return SPM_OK;
+  const int threads = 256;
+  const int blocks = (int)ceil_div<int64_t>((int64_t)kappa * 32, threads);
+  mttkrp_fixup_kernel<<<blocks, threads, 0, s>>>(cta_part, cta_meta, kappa, R, out);
+  SPM_CUDA_TRY(cudaGetLastError());
+  return SPM_OK;
+}
+
 spm_status run_mttkrp(spmttkrp_plan_s* p, int mode, const void* const* factors, float* out,
                       cudaStream_t s) {
   if (!p || mode < 0 || mode >= p->N || !factors || !out) return SPM_ERR_INVALID_ARG;
