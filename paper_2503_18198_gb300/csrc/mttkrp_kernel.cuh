@@ -38,7 +38,13 @@
 
 namespace spm {
 
-constexpr int MT_WARPS = 32;
+#ifndef SPM_MT_PREFETCH
+#define SPM_MT_PREFETCH 0  // steps ahead for L1 prefetch of factor rows (0: off)
+#endif
+#ifndef SPM_MT_WARPS
+#define SPM_MT_WARPS 32
+#endif
+constexpr int MT_WARPS = SPM_MT_WARPS;
 constexpr int MT_THREADS = MT_WARPS * 32;
 #ifndef SPM_MT_STAGES
 #define SPM_MT_STAGES 3
@@ -327,6 +333,27 @@ __global__ void __launch_bounds__(MT_THREADS, 1) mttkrp_kernel(const MttkrpArgs 
         const int nst = (n + G - 1) / G;
         const bool pure = recs[0].x == cur && recs[(n - 1) * RI].x == cur;
         for (int j = 0; j < nst; j += U) {
+#if SPM_MT_PREFETCH > 0
+          // Pull the factor rows of the steps SPM_MT_PREFETCH ahead into L1
+          // (no registers held while they are in flight).
+          if (pure) {
+#pragma unroll
+            for (int uu = 0; uu < U; ++uu) {
+              const int pos = (j + uu + SPM_MT_PREFETCH) * G + slot;
+              if (pos < n) {
+                const int4 r4 = recs[pos * RI];
+                const int cw[3] = {r4.y, r4.z, r4.w};
+#pragma unroll
+                for (int m = 0; m < NPIPE && m < 3; ++m)
+                  if (m < nin) {
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c)
+                      prefetch_l1(static_cast<const FT*>(a.fac[m]) + (int64_t)cw[m] * R + rank0(c));
+                  }
+              }
+            }
+          }
+#endif
           int w[U][W];
           bool valid[U];
           uint32_t y[U][NPIPE][CPL][RAWN];
@@ -478,16 +505,19 @@ __global__ void __launch_bounds__(MT_THREADS, 1) mttkrp_kernel(const MttkrpArgs 
   }
   __syncthreads();
   // inclusive segmented scan of the partials, rows as segment keys
+  // NE * R <= 8192 for every rank (units per partition = clamp(4096/R, 16, 128))
+  constexpr int MERGE_PER_THREAD = (8192 + MT_THREADS - 1) / MT_THREADS;
   for (int d = 1; d < NE; d <<= 1) {
-    float tmp[8];
+    float tmp[MERGE_PER_THREAD];
     int cnt = 0;
-    for (int x = threadIdx.x; x < NE * R; x += MT_THREADS, ++cnt) {
+    for (int x = threadIdx.x; x < NE * R && cnt < MERGE_PER_THREAD; x += MT_THREADS, ++cnt) {
       const int e = x / R;
       tmp[cnt] = (e >= d && prow[e - d] == prow[e]) ? part[x - d * R] : 0.f;
     }
     __syncthreads();
     cnt = 0;
-    for (int x = threadIdx.x; x < NE * R; x += MT_THREADS, ++cnt) part[x] += tmp[cnt];
+    for (int x = threadIdx.x; x < NE * R && cnt < MERGE_PER_THREAD; x += MT_THREADS, ++cnt)
+      part[x] += tmp[cnt];
     __syncthreads();
   }
   // each group's last entry holds the group total
