@@ -178,6 +178,18 @@ def partition_balanced(idx, mode, parts, row_cost=16, perm=None):
     return off
 
 
+def partition_balanced_rows(rows_sorted, parts, row_cost=16):
+    """The same work units from the output-mode indices in copy order (the
+    partition depends only on that non-decreasing sequence)."""
+    lib = _load()
+    rows = np.ascontiguousarray(rows_sorted, dtype=np.int32)
+    off = np.empty(int(parts) + 1, dtype=np.int64)
+    _check(lib.oracle_partition_balanced(int(rows.size), rows.ctypes.data, int(parts),
+                                         int(row_cost), off.ctypes.data),
+           "oracle_partition_balanced")
+    return off
+
+
 def units_from_partitions(off, units):
     """Work units of a partition vector: unit w of partition z starts at
     off[z] + floor((off[z+1] - off[z]) * w / units)."""
