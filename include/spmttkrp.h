@@ -247,6 +247,50 @@ spm_status spmttkrp_run_noalloc(int nmodes, const int64_t *dims, int64_t nnz,
 spm_status cpd_als_step(spmttkrp_plan_t plan, void *const *factors,
                         double *lambda, double *fit, void *stream);
 
+/* ---- batched CP-ALS over many tensors ---------------------------------------- */
+
+/* A batch runs CP-ALS sweeps (Sec. II-A5, as cpd_als_step) over many independent
+ * tensors with one launch per step for all of them: the spMTTKRP of a mode is
+ * one persistent launch whose blocks take (tensor, partition) items from a work
+ * queue (Algorithm 1's partitions of every tensor), and the ALS passes are
+ * launches whose blocks map to (tensor, block) items.  The paper runs one
+ * tensor at a time; grouping the tensors only changes the launch structure:
+ * each tensor keeps its plan, arithmetic and summation order, so its result is
+ * bitwise the one cpd_als_step gives it alone, whatever else is in the batch.
+ *
+ *  plans     host array of ntensors plans, all with the same SPM_FACTOR_* type,
+ *            N in {3, 4}, rank in {8, 16, 32, 64}, policy BALANCED or SCHEME2;
+ *            otherwise SPM_ERR_UNSUPPORTED.  The plans must outlive the batch.
+ *  factors   host array [ntensors * SPM_MAX_MODES]: factors[t*SPM_MAX_MODES+w]
+ *            is tensor t's device factor w (as for cpd_als_step, 16-byte
+ *            aligned); updated in place by every sweep.  Fixed for the batch's
+ *            life.
+ *  lambdas   device double[sum of ranks]: tensor t's weights start at the sum
+ *            of the ranks of tensors 0..t-1.
+ *  fits      device double[ntensors]: fit after each tensor's latest sweep.
+ *  tol, max_sweeps  a tensor stops (is skipped by later sweeps) once
+ *            |fit - previous fit| < tol or it has done max_sweeps sweeps; the
+ *            decision is taken on the device.
+ * Creation computes the Grams of all factors and synchronises `stream`. */
+typedef struct spm_batch_s *spm_batch_t;
+spm_status spm_batch_create(spm_batch_t *out, int ntensors,
+                            const spmttkrp_plan_t *plans, void *const *factors,
+                            double *lambdas, double *fits, double tol,
+                            int max_sweeps, void *stream);
+
+/* One sweep over every still-active tensor.  Launch-only (no host
+ * synchronisation, no allocation): can be captured in a CUDA graph and
+ * replayed. */
+spm_status spm_batch_sweep(spm_batch_t batch, void *stream);
+
+/* Synchronise `stream`; active[t] (host) = 1 while tensor t still iterates,
+ * sweeps[t] (host, may be NULL) = sweeps done. */
+spm_status spm_batch_status(spm_batch_t batch, int *active, int *sweeps,
+                            void *stream);
+
+/* Release the batch (not the plans or the caller's buffers). */
+void spm_batch_destroy(spm_batch_t batch);
+
 /* Synchronise `stream` and return the plan's sticky device-side error
  * (SPM_OK, SPM_ERR_NUMERIC or SPM_ERR_TIMEOUT), then clear it. */
 spm_status spmttkrp_plan_status(spmttkrp_plan_t plan, void *stream);

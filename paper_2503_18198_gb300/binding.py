@@ -50,7 +50,8 @@ SYMBOLS = ("spmttkrp_plan", "spmttkrp_plan_bytes", "spmttkrp_plan_permutation",
            "spmttkrp_plan_partition", "spmttkrp_plan_work_units", "spmttkrp_plan_scheme",
            "spmttkrp_plan_destroy", "spmttkrp_run", "cpd_als_step",
            "spmttkrp_plan_status", "spm_status_string", "spm_device_sm_count",
-           "spmttkrp_run_noalloc")
+           "spmttkrp_run_noalloc", "spm_batch_create", "spm_batch_sweep",
+           "spm_batch_status", "spm_batch_destroy")
 
 
 def library_path() -> str:
@@ -96,6 +97,14 @@ def load(build_if_missing: bool = False):
     lib.spm_status_string.restype = ctypes.c_char_p
     lib.spmttkrp_run_noalloc.argtypes = [i32, P, i64, i32, i32, P, P, u32, P, P]
     lib.spmttkrp_run_noalloc.restype = i32
+    lib.spm_batch_create.argtypes = [P, i32, P, P, P, P, ctypes.c_double, i32, P]
+    lib.spm_batch_create.restype = i32
+    lib.spm_batch_sweep.argtypes = [P, P]
+    lib.spm_batch_sweep.restype = i32
+    lib.spm_batch_status.argtypes = [P, P, P, P]
+    lib.spm_batch_status.restype = i32
+    lib.spm_batch_destroy.argtypes = [P]
+    lib.spm_batch_destroy.restype = None
     lib.spm_device_sm_count.argtypes = []
     lib.spm_device_sm_count.restype = i32
     _lib = lib
@@ -252,3 +261,76 @@ def spmttkrp_run_noalloc(dims, mode: int, rank: int, records, factors, out, flag
                                        ctypes.c_void_p(out.data_ptr()), _stream(stream)),
            "spmttkrp_run_noalloc")
     return out
+
+
+#: largest mode count of the C ABI (factor pointer stride of spm_batch_create)
+SPM_MAX_MODES = 7
+
+
+class Batch:
+    """Owns an spm_batch_t: CP-ALS over many tensors, one launch per step for
+    all of them.  Keeps references to the plans and buffers it was made from."""
+
+    def __init__(self, handle, plans, factors, lambdas, fits):
+        self.handle = handle
+        self.plans = list(plans)
+        self.factors = [list(f) for f in factors]
+        self.lambdas = lambdas
+        self.fits = fits
+        offs = [0]
+        for p in self.plans:
+            offs.append(offs[-1] + p.rank)
+        self.lambda_offsets = offs
+
+    def lam(self, t: int):
+        """Tensor t's weights (a view of the batch's lambda buffer)."""
+        return self.lambdas[self.lambda_offsets[t]:self.lambda_offsets[t + 1]]
+
+    def destroy(self):
+        if self.handle:
+            load().spm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def spm_batch_create(plans, factors, lambdas, fits, tol: float = 0.0, max_sweeps: int = 1,
+                     stream=None) -> Batch:
+    """plans: list of Plan; factors: per tensor the list of its N CUDA factor
+    tensors (updated in place); lambdas: float64 CUDA [sum of ranks];
+    fits: float64 CUDA [len(plans)]."""
+    n = len(plans)
+    hp = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+    fp = (ctypes.c_void_p * (n * SPM_MAX_MODES))()
+    for t, fs in enumerate(factors):
+        for w, f in enumerate(fs):
+            fp[t * SPM_MAX_MODES + w] = f.data_ptr()
+    h = ctypes.c_void_p()
+    _check(load().spm_batch_create(ctypes.byref(h), n, hp, fp,
+                                   ctypes.c_void_p(lambdas.data_ptr()),
+                                   ctypes.c_void_p(fits.data_ptr()), float(tol),
+                                   int(max_sweeps), _stream(stream)),
+           "spm_batch_create")
+    return Batch(h, plans, factors, lambdas, fits)
+
+
+def spm_batch_sweep(batch: Batch, stream=None):
+    """One CP-ALS sweep of every still-active tensor (launches only)."""
+    _check(load().spm_batch_sweep(batch.handle, _stream(stream)), "spm_batch_sweep")
+
+
+def spm_batch_status(batch: Batch, stream=None):
+    """Synchronises; returns (active, sweeps) as lists of ints."""
+    n = len(batch.plans)
+    act = (ctypes.c_int * n)()
+    sw = (ctypes.c_int * n)()
+    _check(load().spm_batch_status(batch.handle, act, sw, _stream(stream)), "spm_batch_status")
+    return list(act), list(sw)
+
+
+def spm_batch_destroy(batch: Batch):
+    batch.destroy()

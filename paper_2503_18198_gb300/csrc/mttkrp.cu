@@ -23,52 +23,16 @@ namespace {
 // Rows without nonzeros (bit clear in `mask`) are written as zeros.
 __global__ void zero_empty_rows_kernel(const uint32_t* __restrict__ mask, int64_t I, int R,
                                        float* __restrict__ out) {
-  const int64_t n = I * R;
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = x / R;
-    if (!((__ldg(&mask[row >> 5]) >> (row & 31)) & 1u)) out[x] = 0.f;
-  }
+  zero_empty_rows_body(mask, R, out, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, I * R,
+                       (int64_t)gridDim.x * blockDim.x);
 }
 
-// One warp per partition z.  If z holds the start of a row that continues
-// into later partitions (its last-row partial), add the first-row partials
-// of the following partitions in partition order and store the row.
+// One warp per partition z (see mttkrp_fixup_body).
 __global__ void __launch_bounds__(256)
     mttkrp_fixup_kernel(const float* __restrict__ cta_part, const int* __restrict__ cta_meta,
                         int kappa, int R, float* __restrict__ out) {
   const int z = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (z >= kappa) return;
-  const int* m = cta_meta + 4 * z;
-  if (!(m[2] & META_PART1)) return;
-  const int row = m[1];
-  float s[8];
-  const float* p1 = cta_part + (int64_t)(2 * z + 1) * R;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int r = lane + 32 * j;
-    s[j] = r < R ? p1[r] : 0.f;
-  }
-  for (int q = z + 1; q < kappa; ++q) {
-    const int* mq = cta_meta + 4 * q;
-    const int fq = mq[2];
-    if (fq & META_EMPTY) continue;
-    if (mq[0] != row) break;
-    const float* p0 = cta_part + (int64_t)(2 * q) * R;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int r = lane + 32 * j;
-      if (r < R) s[j] += p0[r];
-    }
-    if (!(mq[1] == row && (fq & META_SHARED_NEXT))) break;
-  }
-  float* dst = out + (int64_t)row * R;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int r = lane + 32 * j;
-    if (r < R) dst[r] = s[j];
-  }
+  if (z < kappa) mttkrp_fixup_body(cta_part, cta_meta, kappa, R, out, z, threadIdx.x & 31);
 }
 
 }  // namespace

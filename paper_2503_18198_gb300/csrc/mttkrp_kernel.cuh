@@ -38,6 +38,9 @@
 
 namespace spm {
 
+#ifndef SPM_L2_HINTS
+#define SPM_L2_HINTS 0  // 1: records evict-first, factor rows evict-last in L2
+#endif
 #ifndef SPM_MT_PREFETCH
 #define SPM_MT_PREFETCH 0  // steps ahead for L1 prefetch of factor rows (0: off)
 #endif
@@ -96,8 +99,12 @@ struct Slice<float, 4> {
   static constexpr int RAWN = 4;
   static __device__ __forceinline__ void load(const void* base, int64_t row, int R, int r0,
                                               uint32_t* raw) {
+#if SPM_L2_HINTS
+    const uint4 x = ld_nc_v4_hint(static_cast<const float*>(base) + row * R + r0, l2_policy_evict_last());
+#else
     const uint4 x = __ldg(reinterpret_cast<const uint4*>(static_cast<const float*>(base) +
                                                          row * R + r0));
+#endif
     raw[0] = x.x; raw[1] = x.y; raw[2] = x.z; raw[3] = x.w;
   }
   static __device__ __forceinline__ void cvt(const uint32_t* raw, float* f) {
@@ -111,8 +118,13 @@ struct Slice<__nv_bfloat16, 8> {
   static constexpr int RAWN = 4;
   static __device__ __forceinline__ void load(const void* base, int64_t row, int R, int r0,
                                               uint32_t* raw) {
+#if SPM_L2_HINTS
+    const uint4 x = ld_nc_v4_hint(static_cast<const __nv_bfloat16*>(base) + row * R + r0,
+                                  l2_policy_evict_last());
+#else
     const uint4 x = __ldg(reinterpret_cast<const uint4*>(
         static_cast<const __nv_bfloat16*>(base) + row * R + r0));
+#endif
     raw[0] = x.x; raw[1] = x.y; raw[2] = x.z; raw[3] = x.w;
   }
   static __device__ __forceinline__ void cvt(const uint32_t* raw, float* f) {
@@ -167,8 +179,12 @@ __device__ __forceinline__ void store_vec(float* row_ptr, int R, int r0, const f
 // NIN > 0: exactly NIN input modes.  NIN == 0: runtime a.nin (five or more
 // modes); the first two input modes are batched, further ones are fetched
 // when the step is computed.
+//
+// mttkrp_partition processes partition z of one mode copy with the whole
+// thread block (every thread must call it); it is the body of the
+// single-tensor kernel and of the batched persistent kernel.
 template <int RI, int NIN, typename FT, int VEC, int LPN, int CPL>
-__global__ void __launch_bounds__(MT_THREADS, 1) mttkrp_kernel(const MttkrpArgs a) {
+__device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int z) {
   using S = Slice<FT, VEC>;
   constexpr int RAWN = S::RAWN;
   constexpr int G = 32 / LPN;
@@ -191,7 +207,6 @@ __global__ void __launch_bounds__(MT_THREADS, 1) mttkrp_kernel(const MttkrpArgs 
   const int nin = NIN > 0 ? NIN : a.nin;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int slot = lane / LPN, sub = lane % LPN;
-  const int z = blockIdx.x;
   const int64_t* uoff = a.woff + (int64_t)z * NU;
   const int64_t K0 = uoff[0], K1 = uoff[NU];
 
@@ -240,7 +255,12 @@ __global__ void __launch_bounds__(MT_THREADS, 1) mttkrp_kernel(const MttkrpArgs 
         const int q = seq0 + t;
         uint64_t* bar = &bars[q % MT_STAGES];
         mbar_arrive_expect_tx(bar, bytes);
+#if SPM_L2_HINTS
+        bulk_g2s_hint(stages + (q % MT_STAGES) * tile_bytes, a.rec + kb * RI, bytes, bar,
+                      l2_policy_evict_first());
+#else
         bulk_g2s(stages + (q % MT_STAGES) * tile_bytes, a.rec + kb * RI, bytes, bar);
+#endif
       };
       int issued = ntiles < MT_STAGES ? ntiles : MT_STAGES;
       if (lane == 0)
@@ -468,6 +488,10 @@ __global__ void __launch_bounds__(MT_THREADS, 1) mttkrp_kernel(const MttkrpArgs 
     if (lane == 0) nu_next = atomicAdd(&next_unit, 1);
     u = __shfl_sync(SPM_FULL_MASK, nu_next, 0);
   }
+  if (lane == 0 && !timeout) {
+#pragma unroll
+    for (int st = 0; st < MT_STAGES; ++st) mbar_inval(&bars[st]);
+  }
   __syncthreads();
 
   // ---- block merge of the unit-boundary partials ---------------------------
@@ -543,6 +567,60 @@ __global__ void __launch_bounds__(MT_THREADS, 1) mttkrp_kernel(const MttkrpArgs 
     if (shared_next && !(F == L && shared_prev)) flags |= META_PART1;
     meta[0] = F; meta[1] = L; meta[2] = flags; meta[3] = 0;
   }
+}
+
+// Partition fix-up for partition z, one warp (lane = its lane): if z holds
+// the start of a row that continues into later partitions (its last-row
+// partial), add the first-row partials of the following partitions in
+// partition order and store the row.
+__device__ __forceinline__ void mttkrp_fixup_body(const float* __restrict__ cta_part,
+                                                  const int* __restrict__ cta_meta, int kappa,
+                                                  int R, float* __restrict__ out, int z, int lane) {
+  const int* m = cta_meta + 4 * z;
+  if (!(m[2] & META_PART1)) return;
+  const int row = m[1];
+  float s[8];
+  const float* p1 = cta_part + (int64_t)(2 * z + 1) * R;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int r = lane + 32 * j;
+    s[j] = r < R ? p1[r] : 0.f;
+  }
+  for (int q = z + 1; q < kappa; ++q) {
+    const int* mq = cta_meta + 4 * q;
+    const int fq = mq[2];
+    if (fq & META_EMPTY) continue;
+    if (mq[0] != row) break;
+    const float* p0 = cta_part + (int64_t)(2 * q) * R;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int r = lane + 32 * j;
+      if (r < R) s[j] += p0[r];
+    }
+    if (!(mq[1] == row && (fq & META_SHARED_NEXT))) break;
+  }
+  float* dst = out + (int64_t)row * R;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int r = lane + 32 * j;
+    if (r < R) dst[r] = s[j];
+  }
+}
+
+// Rows [x0, x1) of an I x R output whose bit in `mask` is clear are zeroed
+// (x counts elements, not rows).
+__device__ __forceinline__ void zero_empty_rows_body(const uint32_t* __restrict__ mask, int R,
+                                                     float* __restrict__ out, int64_t x0,
+                                                     int64_t x1, int64_t xstep) {
+  for (int64_t x = x0; x < x1; x += xstep) {
+    const int64_t row = x / R;
+    if (!((__ldg(&mask[row >> 5]) >> (row & 31)) & 1u)) out[x] = 0.f;
+  }
+}
+
+template <int RI, int NIN, typename FT, int VEC, int LPN, int CPL>
+__global__ void __launch_bounds__(MT_THREADS, 1) mttkrp_kernel(const MttkrpArgs a) {
+  mttkrp_partition<RI, NIN, FT, VEC, LPN, CPL>(a, blockIdx.x);
 }
 
 }  // namespace spm

@@ -72,6 +72,9 @@ spm_status run_mttkrp(spmttkrp_plan_s* p, int mode, const void* const* factors,
 spm_status als_sweep(spmttkrp_plan_s* p, void* const* factors, double* lambda,
                      double* fit, cudaStream_t s);
 
+// Allocate the plan's CP-ALS workspace on first use (als.cu).
+spm_status ensure_als_state(spmttkrp_plan_s* p);
+
 int sm_count();
 
 }  // namespace spm
