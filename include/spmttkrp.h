@@ -247,6 +247,14 @@ spm_status spmttkrp_run_noalloc(int nmodes, const int64_t *dims, int64_t nnz,
 spm_status cpd_als_step(spmttkrp_plan_t plan, void *const *factors,
                         double *lambda, double *fit, void *stream);
 
+/* Re-run P2 (Sec. III-B) for a new partition count kappa (0 = the SM count,
+ * else 1..65535); the mode copies are kept.  Only for the BALANCED and
+ * SCHEME2 policies (else SPM_ERR_UNSUPPORTED).  Growing kappa beyond the
+ * largest value the plan has had synchronises `stream` and reallocates the
+ * partition arrays.  Results of spmttkrp_run do not depend on kappa beyond
+ * FP32 summation order.  Must not be called while a batch holds the plan. */
+spm_status spmttkrp_plan_repartition(spmttkrp_plan_t plan, int kappa, void *stream);
+
 /* ---- batched CP-ALS over many tensors ---------------------------------------- */
 
 /* A batch runs CP-ALS sweeps (Sec. II-A5, as cpd_als_step) over many independent
@@ -290,6 +298,20 @@ spm_status spm_batch_status(spm_batch_t batch, int *active, int *sweeps,
 
 /* Release the batch (not the plans or the caller's buffers). */
 void spm_batch_destroy(spm_batch_t batch);
+
+/* Autotuner of the batched spMTTKRP: picks the nonzeros per partition.  For
+ * each candidate c (c > 0: every tensor gets kappa = ceil(nnz / c) partitions,
+ * at most 65535; c == 0: one per SM) the plans are repartitioned
+ * (spmttkrp_plan_repartition) and the batched spMTTKRP of all modes is timed
+ * with CUDA events on `stream`, the best of `reps` runs after one warm-up.
+ * The plans are left partitioned for the fastest candidate (*chosen);
+ * ms[c] (host, may be NULL) receives each candidate's time.  Factors: as for
+ * spm_batch_create (read only).  Synchronises `stream`.  Same plan
+ * restrictions as spm_batch_create; no batch may hold the plans meanwhile. */
+spm_status spm_batch_autotune(int ntensors, const spmttkrp_plan_t *plans,
+                              void *const *factors, const int64_t *candidates,
+                              int ncandidates, int reps, int64_t *chosen,
+                              float *ms, void *stream);
 
 /* Synchronise `stream` and return the plan's sticky device-side error
  * (SPM_OK, SPM_ERR_NUMERIC or SPM_ERR_TIMEOUT), then clear it. */

@@ -9,11 +9,12 @@ from .binding import (SPM_FACTOR_BF16, SPM_FACTOR_FP32, SPM_KAPPA,  # noqa: F401
                       SPM_POLICY_ADAPTIVE, SPM_POLICY_BALANCED,
                       SPM_POLICY_SCHEME1, SPM_POLICY_SCHEME2, SPM_ROW_COST,
                       SPM_UNITS_PER_PARTITION, Batch, Plan, SpmError, cpd_als_step,
-                      load, spm_batch_create, spm_batch_destroy, spm_batch_status,
+                      load, spm_batch_autotune, spm_batch_create, spm_batch_destroy, spm_batch_status,
                       spm_batch_sweep,
                       spm_device_sm_count, spm_status_string, spmttkrp_plan,
                       spmttkrp_plan_bytes, spmttkrp_plan_destroy,
                       spmttkrp_plan_partition, spmttkrp_plan_permutation,
-                      spmttkrp_plan_scheme, spmttkrp_plan_status,
+                      spmttkrp_plan_repartition, spmttkrp_plan_scheme,
+                      spmttkrp_plan_status,
                       spmttkrp_plan_work_units, spmttkrp_run,
                       spmttkrp_run_noalloc)

@@ -50,8 +50,8 @@ SYMBOLS = ("spmttkrp_plan", "spmttkrp_plan_bytes", "spmttkrp_plan_permutation",
            "spmttkrp_plan_partition", "spmttkrp_plan_work_units", "spmttkrp_plan_scheme",
            "spmttkrp_plan_destroy", "spmttkrp_run", "cpd_als_step",
            "spmttkrp_plan_status", "spm_status_string", "spm_device_sm_count",
-           "spmttkrp_run_noalloc", "spm_batch_create", "spm_batch_sweep",
-           "spm_batch_status", "spm_batch_destroy")
+           "spmttkrp_run_noalloc", "spmttkrp_plan_repartition", "spm_batch_create", "spm_batch_sweep",
+           "spm_batch_status", "spm_batch_destroy", "spm_batch_autotune")
 
 
 def library_path() -> str:
@@ -97,12 +97,16 @@ def load(build_if_missing: bool = False):
     lib.spm_status_string.restype = ctypes.c_char_p
     lib.spmttkrp_run_noalloc.argtypes = [i32, P, i64, i32, i32, P, P, u32, P, P]
     lib.spmttkrp_run_noalloc.restype = i32
+    lib.spmttkrp_plan_repartition.argtypes = [P, i32, P]
+    lib.spmttkrp_plan_repartition.restype = i32
     lib.spm_batch_create.argtypes = [P, i32, P, P, P, P, ctypes.c_double, i32, P]
     lib.spm_batch_create.restype = i32
     lib.spm_batch_sweep.argtypes = [P, P]
     lib.spm_batch_sweep.restype = i32
     lib.spm_batch_status.argtypes = [P, P, P, P]
     lib.spm_batch_status.restype = i32
+    lib.spm_batch_autotune.argtypes = [i32, P, P, P, i32, i32, P, P, P]
+    lib.spm_batch_autotune.restype = i32
     lib.spm_batch_destroy.argtypes = [P]
     lib.spm_batch_destroy.restype = None
     lib.spm_device_sm_count.argtypes = []
@@ -217,6 +221,12 @@ def spmttkrp_plan_scheme(plan: Plan, mode: int) -> int:
     _check(load().spmttkrp_plan_scheme(plan.handle, int(mode), ctypes.byref(out)),
            "spmttkrp_plan_scheme")
     return int(out.value)
+
+
+def spmttkrp_plan_repartition(plan: Plan, kappa: int, stream=None):
+    """Recompute the partitions for kappa partitions (0 = SM count)."""
+    _check(load().spmttkrp_plan_repartition(plan.handle, int(kappa), _stream(stream)),
+           "spmttkrp_plan_repartition")
 
 
 def spmttkrp_plan_destroy(plan: Plan):
@@ -334,3 +344,22 @@ def spm_batch_status(batch: Batch, stream=None):
 
 def spm_batch_destroy(batch: Batch):
     batch.destroy()
+
+
+def spm_batch_autotune(plans, factors, candidates=(0, 1 << 12, 1 << 14, 1 << 16, 1 << 18),
+                       reps: int = 3, stream=None):
+    """Pick the nonzeros per partition for a batch; returns (chosen, ms per
+    candidate).  The plans are left partitioned for the chosen value."""
+    n = len(plans)
+    hp = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+    fp = (ctypes.c_void_p * (n * SPM_MAX_MODES))()
+    for t, fs in enumerate(factors):
+        for w, f in enumerate(fs):
+            fp[t * SPM_MAX_MODES + w] = f.data_ptr()
+    cand = (ctypes.c_int64 * len(candidates))(*[int(c) for c in candidates])
+    ms = (ctypes.c_float * len(candidates))()
+    chosen = ctypes.c_int64()
+    _check(load().spm_batch_autotune(n, hp, fp, cand, len(candidates), int(reps),
+                                     ctypes.byref(chosen), ms, _stream(stream)),
+           "spm_batch_autotune")
+    return int(chosen.value), list(ms)

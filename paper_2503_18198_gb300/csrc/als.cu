@@ -93,11 +93,11 @@ spm_status launch_gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, 
   return SPM_OK;
 }
 
+}  // namespace
+
 spm_status gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, cudaStream_t s) {
   return p->bf16 ? launch_gram<__nv_bfloat16>(p, Y, I, G, s) : launch_gram<float>(p, Y, I, G, s);
 }
-
-}  // namespace
 
 spm_status ensure_als_state(spmttkrp_plan_s* p) {
   spm_als_state& A = p->als;

@@ -1,41 +1,12 @@
-// batch.cu -- CP-ALS sweeps over many tensors, one launch per step for all
-// of them (see batch_kernels.cuh), and the C ABI of the batch object.
+// batch.cu -- CP-ALS sweeps over a set of tensors with one launch per step
+// for all of them (kernels in batch_kernels.cuh), the nnz-per-partition
+// autotuner, and the C ABI of the batch object.
 #include <algorithm>
 #include <cmath>
 #include <new>
 #include <vector>
 
-#include "batch_kernels.cuh"
-
-struct spm_batch_s {
-  int n = 0;
-  int maxN = 0;
-  bool bf16 = false;
-  int device = 0;
-  std::vector<spmttkrp_plan_s*> plans;
-  std::vector<spm::BatchTensor> host;
-  spm::BatchTensor* bt = nullptr;  // device copy of `host`
-  struct Items {
-    int2* mtt[spm::KC_NONE] = {};
-    int n_mtt[spm::KC_NONE] = {};  // (tensor, partition) per (N, R) class
-    int2* zero = nullptr;
-    int n_zero = 0;  // (tensor, element chunk)
-    int2* tens = nullptr;
-    int n_tens = 0;  // (tensor, 0): tensors that have this mode
-    int2* solve = nullptr;
-    int n_solve = 0;  // (tensor, virtual block)
-    int2* scale = nullptr;
-    int n_scale = 0;
-    int2* gram = nullptr;
-    int n_gram = 0;
-    int2* fit = nullptr;
-    int n_fit = 0;  // tensors whose last mode is this one
-  } items[SPM_MAX_MODES];
-  int* queue = nullptr;  // work-queue counters, one per (mode, class)
-  size_t mtt_smem[spm::KC_NONE] = {};
-  int grid = 0;  // persistent blocks of the MTTKRP launch
-  std::vector<void*> allocs;
-};
+#include "batch.cuh"
 
 namespace spm {
 
@@ -47,7 +18,7 @@ spm_status launch_batch_mttkrp_bf16(int kc, const BatchTensor* bt, const int2* i
 
 namespace {
 
-constexpr int64_t ZERO_CHUNK = 1 << 16;  // output elements per zero-fill item
+constexpr int64_t BATCH_ZERO_CHUNK = 1 << 16;  // output elements per zero-fill item
 
 __global__ void batch_zero_kernel(const BatchTensor* __restrict__ bt, const int2* __restrict__ it,
                                   int mode) {
@@ -55,8 +26,8 @@ __global__ void batch_zero_kernel(const BatchTensor* __restrict__ bt, const int2
   const BatchTensor& b = bt[tc.x];
   if (!b.active) return;
   const int64_t n = b.dims[mode] * b.R;
-  const int64_t x0 = (int64_t)tc.y * ZERO_CHUNK;
-  const int64_t x1 = std::min<int64_t>(n, x0 + ZERO_CHUNK);
+  const int64_t x0 = (int64_t)tc.y * BATCH_ZERO_CHUNK;
+  const int64_t x1 = std::min<int64_t>(n, x0 + BATCH_ZERO_CHUNK);
   zero_empty_rows_body(b.rowmask[mode], b.R, b.M, x0 + threadIdx.x, x1, blockDim.x);
 }
 
@@ -149,38 +120,257 @@ __global__ void __launch_bounds__(ALS_THREADS)
   }
 }
 
+
 template <typename T>
-spm_status upload(spm_batch_s* B, T** dst, const std::vector<T>& v, cudaStream_t s) {
-  *dst = nullptr;
-  if (v.empty()) return SPM_OK;
-  void* p = nullptr;
-  SPM_CUDA_TRY(cudaMalloc(&p, sizeof(T) * v.size()));
-  B->allocs.push_back(p);
-  SPM_CUDA_TRY(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
-  *dst = static_cast<T*>(p);
-  return SPM_OK;
-}
-
-void free_batch(spm_batch_s* B) {
-  if (!B) return;
-  cudaDeviceSynchronize();
-  for (void* p : B->allocs) cudaFree(p);
-  (void)cudaGetLastError();
-  delete B;
-}
-
-// One batched Gram refresh of factor `mode` for every tensor that has it.
-spm_status batch_gram(spm_batch_s* B, int mode, cudaStream_t s) {
-  auto& I = B->items[mode];
-  if (I.n_gram == 0) return SPM_OK;
-  if (B->bf16) batch_gram_kernel<__nv_bfloat16><<<I.n_gram, ALS_THREADS, 0, s>>>(B->bt, I.gram, mode);
-  else batch_gram_kernel<float><<<I.n_gram, ALS_THREADS, 0, s>>>(B->bt, I.gram, mode);
-  batch_gram_reduce_kernel<<<I.n_tens, 256, 0, s>>>(B->bt, I.tens, mode);
-  SPM_CUDA_TRY(cudaGetLastError());
+spm_status grow(T** buf, size_t* cap, size_t need) {
+  if (need <= *cap) return SPM_OK;
+  const size_t n = std::max(need, *cap + *cap / 2);
+  if (*buf) {
+    cudaFree(*buf);  // synchronises the device: queued work is done with it
+    *buf = nullptr;
+    *cap = 0;
+  }
+  cudaError_t e = cudaMalloc((void**)buf, sizeof(T) * n);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    *buf = nullptr;
+    return e == cudaErrorMemoryAllocation ? SPM_ERR_OOM : SPM_ERR_CUDA;
+  }
+  *cap = n;
   return SPM_OK;
 }
 
 }  // namespace
+
+spm_status batch_add(spm_batch_s* B, spmttkrp_plan_s* p, void* const* factors, double* lambda,
+                     double* fit, double tol, int max_sweeps, cudaStream_t s) {
+  if (!p || !factors || !lambda || !fit || max_sweeps < 1 || !(tol >= 0.0))
+    return SPM_ERR_INVALID_ARG;
+  const int kc = batch_kclass(p->N, p->R);
+  if (kc == KC_NONE || (B->bf16 >= 0 && B->bf16 != (int)p->bf16)) return SPM_ERR_UNSUPPORTED;
+  for (int d = 0; d < p->N; ++d)
+    if (p->mode[d].scheme == 1) return SPM_ERR_UNSUPPORTED;
+  for (int w = 0; w < p->N; ++w)
+    if (!factors[w] || (reinterpret_cast<uintptr_t>(factors[w]) & 15u)) return SPM_ERR_INVALID_ARG;
+  for (const spmttkrp_plan_s* q : B->plans)
+    if (q == p) return SPM_ERR_INVALID_ARG;  // one batch slot per plan (shared workspace)
+  // the members' convergence state lives on the device between sweeps
+  if (!B->dirty) SPM_TRY(batch_pull(B, s));
+  SPM_TRY(ensure_als_state(p));
+  spm_als_state& A = p->als;
+  A.ready = false;  // the batch keeps the Grams from now on
+  BatchTensor b{};
+  b.N = p->N;
+  b.R = p->R;
+  b.kappa = p->kappa;
+  b.kclass = kc;
+  b.gram = A.gram;
+  b.gram_part = A.gram_part;
+  b.chol = A.chol;
+  b.winv = A.winv;
+  b.colsq_part = A.colsq_part;
+  b.inner_part = A.inner_part;
+  b.lambda_ws = A.lambda_ws;
+  b.M = A.M;
+  b.Z = A.Z;
+  b.normX2 = p->normX2;
+  b.err = p->dev_err;
+  b.lambda_out = lambda;
+  b.fit_out = fit;
+  b.active = 1;
+  b.sweeps = 0;
+  b.max_sweeps = max_sweeps;
+  b.tol = tol;
+  b.prev_fit = -1.0e300;
+  for (int w = 0; w < p->N; ++w) b.fac[w] = factors[w];
+  for (int d = 0; d < p->N; ++d) {
+    const int64_t I = p->dims[d];
+    b.dims[d] = I;
+    b.rowmask[d] = p->mode[d].rowmask;
+    MttkrpArgs& a = b.margs[d];
+    a = MttkrpArgs{};
+    a.rec = p->mode[d].rec;
+    a.woff = p->mode[d].woff;
+    int m = 0;
+    for (int w = 0; w < p->N; ++w)
+      if (w != d) a.fac[m++] = b.fac[w];
+    a.out = A.M;
+    a.cta_part = p->cta_part;  // the modes run one after another: one workspace
+    a.cta_meta = p->cta_meta;
+    a.err = p->dev_err;
+    a.nnz = p->nnz;
+    a.I = I;
+    a.R = p->R;
+    a.nin = p->N - 1;
+    a.nu = p->nu;
+    // the single-tensor sweep's virtual block counts (identical sums)
+    b.nb_gram[d] = work_blocks(I, GRAM_TILE_ROWS, A.gram_blocks);
+    b.gram_rpb[d] = ceil_div<int64_t>(I, b.nb_gram[d]);
+    b.nb_solve[d] = work_blocks(I, 4 * (ALS_THREADS / 32), A.gram_blocks);
+    b.nb_scale[d] = work_blocks(I, ALS_THREADS / p->R, A.gram_blocks);
+  }
+  for (int w = 0; w < p->N; ++w)
+    SPM_TRY(gram(p, factors[w], p->dims[w], A.gram + (size_t)w * p->R * p->R, s));
+  B->plans.push_back(p);
+  B->host.push_back(b);
+  B->bf16 = p->bf16 ? 1 : 0;
+  B->dirty = true;
+  return SPM_OK;
+}
+
+void batch_remove(spm_batch_s* B, int t) {
+  B->plans.erase(B->plans.begin() + t);
+  B->host.erase(B->host.begin() + t);
+  if (B->plans.empty()) B->bf16 = -1;
+  B->dirty = true;
+}
+
+spm_status batch_pull(spm_batch_s* B, cudaStream_t s) {
+  if (B->bt && !B->host.empty() && !B->dirty)
+    SPM_CUDA_TRY(cudaMemcpyAsync(B->host.data(), B->bt, sizeof(BatchTensor) * B->host.size(),
+                                 cudaMemcpyDeviceToHost, s));
+  SPM_CUDA_TRY(cudaStreamSynchronize(s));
+  return SPM_OK;
+}
+
+spm_status batch_commit(spm_batch_s* B, cudaStream_t s) {
+  if (!B->dirty) return SPM_OK;
+  const int n = (int)B->host.size();
+  B->maxN = 0;
+  for (int kc = 0; kc < KC_NONE; ++kc) B->mtt_smem[kc] = 0;
+  for (int t = 0; t < n; ++t) {
+    const spmttkrp_plan_s* p = B->plans[t];
+    B->maxN = std::max(B->maxN, p->N);
+    // partitions may have changed since the tensor was added (autotuning)
+    B->host[t].kappa = p->kappa;
+    for (int d = 0; d < p->N; ++d) B->host[t].margs[d].woff = p->mode[d].woff;
+    const int kc = B->host[t].kclass;
+    B->mtt_smem[kc] =
+        std::max(B->mtt_smem[kc], mttkrp_smem_bytes(p->R, record_int4s(p->N), p->nu));
+  }
+  std::vector<int2>& v = B->stage;
+  v.clear();
+  for (int d = 0; d < SPM_MAX_MODES; ++d) {
+    spm_batch_s::ModeItems& I = B->mi[d];
+    I = spm_batch_s::ModeItems{};
+    for (int kc = 0; kc < KC_NONE; ++kc) {
+      I.mtt_off[kc] = (int)v.size();
+      for (int t = 0; t < n; ++t) {
+        const spmttkrp_plan_s* p = B->plans[t];
+        if (d < p->N && B->host[t].kclass == kc && p->nnz > 0)
+          for (int z = 0; z < p->kappa; ++z) v.push_back(make_int2(t, z));
+      }
+      I.n_mtt[kc] = (int)v.size() - I.mtt_off[kc];
+    }
+    I.zero_off = (int)v.size();
+    for (int t = 0; t < n; ++t) {
+      const spmttkrp_plan_s* p = B->plans[t];
+      // an empty tensor has no partition items: its row masks are all
+      // clear, so the zero-fill items cover its whole output
+      if (d < p->N && (p->nnz == 0 || p->mode[d].empty_rows > 0)) {
+        const int64_t chunks = ceil_div<int64_t>(p->dims[d] * p->R, BATCH_ZERO_CHUNK);
+        for (int64_t c = 0; c < chunks; ++c) v.push_back(make_int2(t, (int)c));
+      }
+    }
+    I.n_zero = (int)v.size() - I.zero_off;
+    auto per_tensor = [&](int* off, int* cnt, auto count) {
+      *off = (int)v.size();
+      for (int t = 0; t < n; ++t) {
+        if (d >= B->plans[t]->N) continue;
+        const int k = count(t);
+        for (int j = 0; j < k; ++j) v.push_back(make_int2(t, j));
+      }
+      *cnt = (int)v.size() - *off;
+    };
+    per_tensor(&I.tens_off, &I.n_tens, [&](int) { return 1; });
+    per_tensor(&I.solve_off, &I.n_solve, [&](int t) { return B->host[t].nb_solve[d]; });
+    per_tensor(&I.scale_off, &I.n_scale, [&](int t) { return B->host[t].nb_scale[d]; });
+    per_tensor(&I.gram_off, &I.n_gram, [&](int t) { return B->host[t].nb_gram[d]; });
+    per_tensor(&I.fit_off, &I.n_fit, [&](int t) { return d == B->plans[t]->N - 1 ? 1 : 0; });
+  }
+  SPM_TRY(grow(&B->bt, &B->bt_cap, std::max<size_t>(1, n)));
+  SPM_TRY(grow(&B->items, &B->items_cap, std::max<size_t>(1, v.size())));
+  if (!B->queue) SPM_CUDA_TRY(cudaMalloc((void**)&B->queue, sizeof(int) * SPM_MAX_MODES * KC_NONE));
+  if (n > 0)
+    SPM_CUDA_TRY(cudaMemcpyAsync(B->bt, B->host.data(), sizeof(BatchTensor) * n,
+                                 cudaMemcpyHostToDevice, s));
+  if (!v.empty())
+    SPM_CUDA_TRY(cudaMemcpyAsync(B->items, v.data(), sizeof(int2) * v.size(),
+                                 cudaMemcpyHostToDevice, s));
+  for (int kc = 0; kc < KC_NONE; ++kc) {
+    if (B->mtt_smem[kc] == 0 || B->mtt_smem[kc] <= B->smem_set[kc]) continue;
+    SPM_TRY(B->bf16 == 1 ? launch_batch_mttkrp_bf16(kc, nullptr, nullptr, 0, nullptr, 0, 0,
+                                                    B->mtt_smem[kc], s)
+                         : launch_batch_mttkrp_f32(kc, nullptr, nullptr, 0, nullptr, 0, 0,
+                                                   B->mtt_smem[kc], s));
+    B->smem_set[kc] = B->mtt_smem[kc];
+  }
+  if (B->grid == 0) B->grid = std::max(1, sm_count());
+  // the staged host vectors must outlive the asynchronous copies
+  SPM_CUDA_TRY(cudaStreamSynchronize(s));
+  B->dirty = false;
+  return SPM_OK;
+}
+
+spm_status batch_mttkrp(spm_batch_s* B, int d, cudaStream_t s) {
+  const spm_batch_s::ModeItems& I = B->mi[d];
+  if (I.n_zero > 0) batch_zero_kernel<<<I.n_zero, 256, 0, s>>>(B->bt, B->items + I.zero_off, d);
+  int* q = B->queue + d * KC_NONE;
+  SPM_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(int) * KC_NONE, s));
+  for (int kc = 0; kc < KC_NONE; ++kc) {
+    const int n = I.n_mtt[kc];
+    if (n == 0) continue;
+    const int grid = std::min(B->grid, n);
+    const int2* it = B->items + I.mtt_off[kc];
+    SPM_TRY(B->bf16 == 1
+                ? launch_batch_mttkrp_bf16(kc, B->bt, it, n, q + kc, d, grid, B->mtt_smem[kc], s)
+                : launch_batch_mttkrp_f32(kc, B->bt, it, n, q + kc, d, grid, B->mtt_smem[kc], s));
+  }
+  for (int kc = 0; kc < KC_NONE; ++kc) {
+    const int n = I.n_mtt[kc];
+    if (n == 0) continue;
+    batch_fixup_kernel<<<(int)ceil_div<int64_t>((int64_t)n * 32, 256), 256, 0, s>>>(
+        B->bt, B->items + I.mtt_off[kc], n, d);
+  }
+  SPM_CUDA_TRY(cudaGetLastError());
+  return SPM_OK;
+}
+
+spm_status batch_sweep(spm_batch_s* B, cudaStream_t s) {
+  SPM_TRY(batch_commit(B, s));
+  if (B->host.empty()) return SPM_OK;
+  const int2* it = B->items;
+  for (int d = 0; d < B->maxN; ++d) {
+    const spm_batch_s::ModeItems& I = B->mi[d];
+    SPM_TRY(batch_mttkrp(B, d, s));
+    batch_system_kernel<<<I.n_tens, ALS_THREADS, 0, s>>>(B->bt, it + I.tens_off, d);
+    batch_solve_kernel<<<I.n_solve, ALS_THREADS, 0, s>>>(B->bt, it + I.solve_off, d);
+    batch_lambda_kernel<<<I.n_tens, 256, 0, s>>>(B->bt, it + I.tens_off, d);
+    if (B->bf16 == 1)
+      batch_scale_kernel<__nv_bfloat16><<<I.n_scale, ALS_THREADS, 0, s>>>(B->bt, it + I.scale_off, d);
+    else
+      batch_scale_kernel<float><<<I.n_scale, ALS_THREADS, 0, s>>>(B->bt, it + I.scale_off, d);
+    if (B->bf16 == 1)
+      batch_gram_kernel<__nv_bfloat16><<<I.n_gram, ALS_THREADS, 0, s>>>(B->bt, it + I.gram_off, d);
+    else
+      batch_gram_kernel<float><<<I.n_gram, ALS_THREADS, 0, s>>>(B->bt, it + I.gram_off, d);
+    batch_gram_reduce_kernel<<<I.n_tens, 256, 0, s>>>(B->bt, it + I.tens_off, d);
+    if (I.n_fit > 0) batch_fit_kernel<<<I.n_fit, ALS_THREADS, 0, s>>>(B->bt, it + I.fit_off, d);
+    SPM_CUDA_TRY(cudaGetLastError());
+  }
+  return SPM_OK;
+}
+
+void batch_free(spm_batch_s* B) {
+  if (!B) return;
+  cudaDeviceSynchronize();
+  if (B->bt) cudaFree(B->bt);
+  if (B->items) cudaFree(B->items);
+  if (B->queue) cudaFree(B->queue);
+  (void)cudaGetLastError();
+  delete B;
+}
+
 }  // namespace spm
 
 using namespace spm;
@@ -195,144 +385,26 @@ spm_status spm_batch_create(spm_batch_t* out, int ntensors, const spmttkrp_plan_
   if (ntensors < 1 || !plans || !factors || !lambdas || !fits || max_sweeps < 1 || !(tol >= 0.0))
     return SPM_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const bool bf16 = plans[0] && plans[0]->bf16;
   for (int t = 0; t < ntensors; ++t) {
     const spmttkrp_plan_s* p = plans[t];
     if (!p) return SPM_ERR_INVALID_ARG;
-    if (p->bf16 != bf16 || batch_kclass(p->N, p->R) == KC_NONE) return SPM_ERR_UNSUPPORTED;
-    for (int d = 0; d < p->N; ++d)
-      if (p->mode[d].scheme == 1) return SPM_ERR_UNSUPPORTED;
-    for (int w = 0; w < p->N; ++w) {
-      const void* f = factors[(size_t)t * SPM_MAX_MODES + w];
-      if (!f || (reinterpret_cast<uintptr_t>(f) & 15u)) return SPM_ERR_INVALID_ARG;
-    }
+    if (p->bf16 != plans[0]->bf16 || batch_kclass(p->N, p->R) == KC_NONE) return SPM_ERR_UNSUPPORTED;
   }
   spm_batch_s* B = new (std::nothrow) spm_batch_s();
   if (!B) return SPM_ERR_OOM;
   cudaGetDevice(&B->device);
-  B->n = ntensors;
-  B->bf16 = bf16;
-  B->plans.assign(plans, plans + ntensors);
-  B->host.resize(ntensors);
-  std::vector<int2> mtt[SPM_MAX_MODES][KC_NONE], zero[SPM_MAX_MODES], tens[SPM_MAX_MODES],
-      solve[SPM_MAX_MODES], scale[SPM_MAX_MODES], gram[SPM_MAX_MODES], fit[SPM_MAX_MODES];
-  size_t lam_off = 0;
   spm_status st = SPM_OK;
+  size_t lam_off = 0;
   for (int t = 0; t < ntensors && st == SPM_OK; ++t) {
-    spmttkrp_plan_s* p = plans[t];
-    st = ensure_als_state(p);
-    if (st != SPM_OK) break;
-    spm_als_state& A = p->als;
-    A.ready = false;  // the batch owns the Grams from now on
-    BatchTensor& b = B->host[t];
-    b = BatchTensor{};
-    b.N = p->N;
-    b.R = p->R;
-    b.kappa = p->kappa;
-    b.kclass = batch_kclass(p->N, p->R);
-    B->maxN = std::max(B->maxN, p->N);
-    b.gram = A.gram;
-    b.gram_part = A.gram_part;
-    b.chol = A.chol;
-    b.winv = A.winv;
-    b.colsq_part = A.colsq_part;
-    b.inner_part = A.inner_part;
-    b.lambda_ws = A.lambda_ws;
-    b.M = A.M;
-    b.Z = A.Z;
-    b.normX2 = p->normX2;
-    b.err = p->dev_err;
-    b.lambda_out = lambdas + lam_off;
-    lam_off += (size_t)p->R;
-    b.fit_out = fits + t;
-    b.active = 1;
-    b.sweeps = 0;
-    b.max_sweeps = max_sweeps;
-    b.tol = tol;
-    b.prev_fit = -1.0e300;
-    for (int w = 0; w < p->N; ++w) b.fac[w] = factors[(size_t)t * SPM_MAX_MODES + w];
-    for (int d = 0; d < p->N; ++d) {
-      const int64_t I = p->dims[d];
-      b.dims[d] = I;
-      b.rowmask[d] = p->mode[d].rowmask;
-      MttkrpArgs& a = b.margs[d];
-      a = MttkrpArgs{};
-      a.rec = p->mode[d].rec;
-      a.woff = p->mode[d].woff;
-      int m = 0;
-      for (int w = 0; w < p->N; ++w)
-        if (w != d) a.fac[m++] = b.fac[w];
-      a.out = A.M;
-      a.cta_part = p->cta_part;  // modes run one after another: the workspace is reused
-      a.cta_meta = p->cta_meta;
-      a.err = p->dev_err;
-      a.nnz = p->nnz;
-      a.I = I;
-      a.R = p->R;
-      a.nin = p->N - 1;
-      a.nu = p->nu;
-      // same virtual block counts as the single-tensor sweep (identical sums)
-      b.nb_gram[d] = work_blocks(I, GRAM_TILE_ROWS, A.gram_blocks);
-      b.gram_rpb[d] = ceil_div<int64_t>(I, b.nb_gram[d]);
-      b.nb_solve[d] = work_blocks(I, 4 * (ALS_THREADS / 32), A.gram_blocks);
-      b.nb_scale[d] = work_blocks(I, ALS_THREADS / p->R, A.gram_blocks);
-      if (p->nnz > 0)
-        for (int z = 0; z < p->kappa; ++z) mtt[d][b.kclass].push_back(make_int2(t, z));
-      if (p->nnz == 0 || p->mode[d].empty_rows > 0) {
-        const int64_t chunks = ceil_div<int64_t>(I * p->R, ZERO_CHUNK);
-        for (int64_t c = 0; c < chunks; ++c) zero[d].push_back(make_int2(t, (int)c));
-      }
-      tens[d].push_back(make_int2(t, 0));
-      for (int v = 0; v < b.nb_solve[d]; ++v) solve[d].push_back(make_int2(t, v));
-      for (int v = 0; v < b.nb_scale[d]; ++v) scale[d].push_back(make_int2(t, v));
-      for (int v = 0; v < b.nb_gram[d]; ++v) gram[d].push_back(make_int2(t, v));
-      if (d == p->N - 1) fit[d].push_back(make_int2(t, 0));
-      B->mtt_smem[b.kclass] = std::max(B->mtt_smem[b.kclass],
-                                       mttkrp_smem_bytes(p->R, record_int4s(p->N), p->nu));
-    }
-    // an empty tensor has no partition items: its row masks are all clear,
-    // so the zero-fill items cover its whole output
+    st = batch_add(B, plans[t], factors + (size_t)t * SPM_MAX_MODES, lambdas + lam_off, fits + t,
+                   tol, max_sweeps, s);
+    lam_off += (size_t)plans[t]->R;
   }
-  for (int d = 0; d < SPM_MAX_MODES && st == SPM_OK; ++d) {
-    auto& I = B->items[d];
-    I.n_zero = (int)zero[d].size();
-    I.n_tens = (int)tens[d].size();
-    I.n_solve = (int)solve[d].size();
-    I.n_scale = (int)scale[d].size();
-    I.n_gram = (int)gram[d].size();
-    I.n_fit = (int)fit[d].size();
-    for (int kc = 0; kc < KC_NONE; ++kc) {
-      I.n_mtt[kc] = (int)mtt[d][kc].size();
-      if (st == SPM_OK) st = upload(B, &I.mtt[kc], mtt[d][kc], s);
-    }
-    if (st == SPM_OK) st = upload(B, &I.zero, zero[d], s);
-    if (st == SPM_OK) st = upload(B, &I.tens, tens[d], s);
-    if (st == SPM_OK) st = upload(B, &I.solve, solve[d], s);
-    if (st == SPM_OK) st = upload(B, &I.scale, scale[d], s);
-    if (st == SPM_OK) st = upload(B, &I.gram, gram[d], s);
-    if (st == SPM_OK) st = upload(B, &I.fit, fit[d], s);
-  }
-  if (st == SPM_OK) st = upload(B, &B->bt, B->host, s);
-  if (st == SPM_OK) {
-    void* q = nullptr;
-    if (cudaMalloc(&q, sizeof(int) * SPM_MAX_MODES * KC_NONE) != cudaSuccess) st = SPM_ERR_OOM;
-    else {
-      B->allocs.push_back(q);
-      B->queue = static_cast<int*>(q);
-    }
-  }
-  B->grid = std::max(1, sm_count());
-  // kernel attributes once, so that a sweep only launches (graph capture)
-  for (int kc = 0; kc < KC_NONE && st == SPM_OK; ++kc)
-    if (B->mtt_smem[kc] > 0)
-      st = bf16 ? launch_batch_mttkrp_bf16(kc, nullptr, nullptr, 0, nullptr, 0, 0, B->mtt_smem[kc], s)
-                : launch_batch_mttkrp_f32(kc, nullptr, nullptr, 0, nullptr, 0, 0, B->mtt_smem[kc], s);
-  // initial Grams of every factor
-  for (int w = 0; w < B->maxN && st == SPM_OK; ++w) st = batch_gram(B, w, s);
+  if (st == SPM_OK) st = batch_commit(B, s);
   if (st == SPM_OK && cudaStreamSynchronize(s) != cudaSuccess) st = SPM_ERR_CUDA;
   if (st != SPM_OK) {
     (void)cudaGetLastError();
-    free_batch(B);
+    batch_free(B);
     return st;
   }
   *out = B;
@@ -341,52 +413,84 @@ spm_status spm_batch_create(spm_batch_t* out, int ntensors, const spmttkrp_plan_
 
 spm_status spm_batch_sweep(spm_batch_t B, void* stream) {
   if (!B) return SPM_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  for (int d = 0; d < B->maxN; ++d) {
-    auto& I = B->items[d];
-    if (I.n_zero > 0) batch_zero_kernel<<<I.n_zero, 256, 0, s>>>(B->bt, I.zero, d);
-    int* q = B->queue + d * KC_NONE;
-    SPM_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(int) * KC_NONE, s));
-    for (int kc = 0; kc < KC_NONE; ++kc) {
-      const int n = I.n_mtt[kc];
-      if (n == 0) continue;
-      const int grid = std::min(B->grid, n);
-      SPM_TRY(B->bf16 ? launch_batch_mttkrp_bf16(kc, B->bt, I.mtt[kc], n, q + kc, d, grid,
-                                                 B->mtt_smem[kc], s)
-                      : launch_batch_mttkrp_f32(kc, B->bt, I.mtt[kc], n, q + kc, d, grid,
-                                                B->mtt_smem[kc], s));
-    }
-    for (int kc = 0; kc < KC_NONE; ++kc) {
-      const int n = I.n_mtt[kc];
-      if (n == 0) continue;
-      batch_fixup_kernel<<<(int)ceil_div<int64_t>((int64_t)n * 32, 256), 256, 0, s>>>(
-          B->bt, I.mtt[kc], n, d);
-    }
-    batch_system_kernel<<<I.n_tens, ALS_THREADS, 0, s>>>(B->bt, I.tens, d);
-    batch_solve_kernel<<<I.n_solve, ALS_THREADS, 0, s>>>(B->bt, I.solve, d);
-    batch_lambda_kernel<<<I.n_tens, 256, 0, s>>>(B->bt, I.tens, d);
-    if (B->bf16) batch_scale_kernel<__nv_bfloat16><<<I.n_scale, ALS_THREADS, 0, s>>>(B->bt, I.scale, d);
-    else batch_scale_kernel<float><<<I.n_scale, ALS_THREADS, 0, s>>>(B->bt, I.scale, d);
-    SPM_TRY(batch_gram(B, d, s));
-    if (I.n_fit > 0) batch_fit_kernel<<<I.n_fit, ALS_THREADS, 0, s>>>(B->bt, I.fit, d);
-    SPM_CUDA_TRY(cudaGetLastError());
-  }
-  return SPM_OK;
+  return batch_sweep(B, static_cast<cudaStream_t>(stream));
 }
 
 spm_status spm_batch_status(spm_batch_t B, int* active, int* sweeps, void* stream) {
   if (!B || !active) return SPM_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  SPM_CUDA_TRY(cudaMemcpyAsync(B->host.data(), B->bt, sizeof(BatchTensor) * B->n,
-                               cudaMemcpyDeviceToHost, s));
-  SPM_CUDA_TRY(cudaStreamSynchronize(s));
-  for (int t = 0; t < B->n; ++t) {
+  SPM_TRY(batch_pull(B, static_cast<cudaStream_t>(stream)));
+  for (size_t t = 0; t < B->host.size(); ++t) {
     active[t] = B->host[t].active;
     if (sweeps) sweeps[t] = B->host[t].sweeps;
   }
   return SPM_OK;
 }
 
-void spm_batch_destroy(spm_batch_t B) { free_batch(B); }
+void spm_batch_destroy(spm_batch_t B) { batch_free(B); }
+
+spm_status spm_batch_autotune(int ntensors, const spmttkrp_plan_t* plans, void* const* factors,
+                              const int64_t* candidates, int ncandidates, int reps,
+                              int64_t* chosen, float* ms, void* stream) {
+  if (ntensors < 1 || !plans || !factors || !candidates || ncandidates < 1 || reps < 1 || !chosen)
+    return SPM_ERR_INVALID_ARG;
+  for (int c = 0; c < ncandidates; ++c)
+    if (candidates[c] < 0) return SPM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int sms = std::max(1, sm_count());
+  auto kappa_for = [&](const spmttkrp_plan_s* p, int64_t target) -> int {
+    if (target == 0) return sms;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(0xFFFF, ceil_div<int64_t>(p->nnz, target)));
+  };
+  // scratch weights and fits for the timing batches
+  size_t rsum = 0;
+  for (int t = 0; t < ntensors; ++t) {
+    if (!plans[t]) return SPM_ERR_INVALID_ARG;
+    rsum += (size_t)plans[t]->R;
+  }
+  double* scratch = nullptr;
+  SPM_CUDA_TRY(cudaMalloc((void**)&scratch, sizeof(double) * (rsum + ntensors)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  spm_status st = SPM_OK;
+  float best_ms = 0.f;
+  int best = -1;
+  for (int c = 0; c < ncandidates && st == SPM_OK; ++c) {
+    for (int t = 0; t < ntensors && st == SPM_OK; ++t)
+      st = plan_repartition(plans[t], kappa_for(plans[t], candidates[c]), s);
+    spm_batch_s* B = nullptr;
+    if (st == SPM_OK)
+      st = spm_batch_create(&B, ntensors, plans, factors, scratch, scratch + rsum, 0.0, 1, stream);
+    float t_min = 0.f;
+    for (int r = 0; r <= reps && st == SPM_OK; ++r) {  // r == 0 warms up
+      cudaEventRecord(e0, s);
+      for (int d = 0; d < B->maxN && st == SPM_OK; ++d) st = batch_mttkrp(B, d, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = SPM_ERR_CUDA;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r == 1 || (r > 1 && t < t_min)) t_min = t;
+    }
+    if (B) batch_free(B);
+    if (st != SPM_OK) break;
+    if (ms) ms[c] = t_min;
+    if (best < 0 || t_min < best_ms) {
+      best_ms = t_min;
+      best = c;
+    }
+  }
+  if (st == SPM_OK) {
+    for (int t = 0; t < ntensors && st == SPM_OK; ++t)
+      st = plan_repartition(plans[t], kappa_for(plans[t], candidates[best]), s);
+    *chosen = candidates[best];
+  }
+  for (int t = 0; t < ntensors; ++t) plans[t]->als.ready = false;
+  if (st == SPM_OK && cudaStreamSynchronize(s) != cudaSuccess) st = SPM_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(scratch);
+  (void)cudaGetLastError();
+  return st;
+}
 
 }  // extern "C"

@@ -18,8 +18,28 @@ spm_status plan_alloc(spmttkrp_plan_s* p, void** ptr, size_t bytes) {
     *ptr = nullptr;
     return e == cudaErrorMemoryAllocation ? SPM_ERR_OOM : SPM_ERR_CUDA;
   }
+  p->alloc_bytes[p->nallocs] = bytes;
   p->allocs[p->nallocs++] = *ptr;
   p->bytes += bytes;
+  return SPM_OK;
+}
+
+spm_status plan_realloc(spmttkrp_plan_s* p, void** ptr, size_t bytes) {
+  int i = 0;
+  while (i < p->nallocs && p->allocs[i] != *ptr) ++i;
+  if (i == p->nallocs) return SPM_ERR_INVALID_ARG;
+  if (bytes == 0) bytes = 16;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? SPM_ERR_OOM : SPM_ERR_CUDA;
+  }
+  cudaFree(*ptr);
+  p->bytes = p->bytes - p->alloc_bytes[i] + bytes;
+  p->allocs[i] = q;
+  p->alloc_bytes[i] = bytes;
+  *ptr = q;
   return SPM_OK;
 }
 
@@ -108,6 +128,7 @@ spm_status spmttkrp_plan(spmttkrp_plan_t* out, int nmodes, const int64_t* dims, 
   p->flags = flags;
   p->bf16 = (flags & SPM_FACTOR_MASK) == SPM_FACTOR_BF16;
   p->kappa = kappa;
+  p->kappa_cap = kappa;
   p->nu = SPM_UNITS_PER_PARTITION(rank);
   p->policy = policy;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -169,6 +190,12 @@ spm_status spmttkrp_plan_scheme(spmttkrp_plan_t plan, int mode, int* scheme) {
   if (!plan || mode < 0 || mode >= plan->N || !scheme) return SPM_ERR_INVALID_ARG;
   *scheme = plan->mode[mode].scheme;
   return SPM_OK;
+}
+
+spm_status spmttkrp_plan_repartition(spmttkrp_plan_t plan, int kappa, void* stream) {
+  if (!plan) return SPM_ERR_INVALID_ARG;
+  if (kappa == 0) kappa = sm_count();
+  return plan_repartition(plan, kappa, static_cast<cudaStream_t>(stream));
 }
 
 void spmttkrp_plan_destroy(spmttkrp_plan_t plan) {

@@ -569,6 +569,34 @@ int bits_for(int64_t dim) {
 
 constexpr int NORM_BLOCKS = 1024;
 
+// P2 for a copy under the cost-balanced policy (scheme 0) or Scheme 2, and
+// for an empty tensor under any policy: partition offsets off[0..kappa] and
+// work-unit offsets woff[0..kappa*nu].  Scratch: hist >= ceil(nnz/RS_TILE)
+// words, dtot >= 1 word, before >= nnz words.
+template <int RI>
+void partition_copy(spmttkrp_plan_s* p, int d, uint32_t* hist, uint32_t* dtot, uint32_t* before,
+                    cudaStream_t s) {
+  const int T = 256;
+  const int64_t n = p->nnz;
+  const int units = p->nu;
+  const int64_t P = (int64_t)p->kappa * units;
+  spm_mode_copy& c = p->mode[d];
+  if (c.scheme == 0 && n > 0) {
+    // cost-balanced work units over the copy order
+    const int nb = (int)ceil_div<int64_t>(n, RS_TILE);
+    head_count_kernel<RI><<<nb, RS_THREADS, 0, s>>>(c.rec, n, hist);
+    rs_scan_rows_kernel<<<1, 1024, 0, s>>>(hist, nb, dtot);
+    head_prefix_kernel<RI><<<nb, RS_THREADS, 0, s>>>(c.rec, n, hist, before);
+    balanced_units_kernel<<<grid_for(P + 1, T), T, 0, s>>>(before, dtot, n, P, SPM_ROW_COST,
+                                                          c.woff);
+    partitions_from_units_kernel<<<grid_for(p->kappa + 1, T), T, 0, s>>>(c.woff, p->kappa,
+                                                                        units, c.off);
+    return;
+  }
+  equal_offsets_kernel<<<grid_for(p->kappa + 1, T), T, 0, s>>>(n, p->kappa, c.off);
+  units_from_partitions_kernel<<<grid_for(P + 1, T), T, 0, s>>>(c.off, p->kappa, units, c.woff);
+}
+
 template <int RI>
 spm_status build_copies_t(spmttkrp_plan_s* p, const int32_t* const* idx_in, const float* vals,
                           cudaStream_t s) {
@@ -691,23 +719,8 @@ spm_status build_copies_t(spmttkrp_plan_s* p, const int32_t* const* idx_in, cons
     if (p->policy == (int)(SPM_POLICY_SCHEME1 >> 4)) scheme = 1;
     if (p->policy == (int)(SPM_POLICY_ADAPTIVE >> 4)) scheme = p->dims[d] >= p->kappa ? 1 : 2;
     c.scheme = scheme;
-    if (scheme == 0 && n > 0) {
-      // cost-balanced work units over the copy order
-      const int nb = (int)ceil_div<int64_t>(n, RS_TILE);
-      uint32_t* before = reinterpret_cast<uint32_t*>(va);  // n entries
-      head_count_kernel<RI><<<nb, RS_THREADS, 0, s>>>(c.rec, n, sc.hist);
-      rs_scan_rows_kernel<<<1, 1024, 0, s>>>(sc.hist, nb, sc.dtot);
-      head_prefix_kernel<RI><<<nb, RS_THREADS, 0, s>>>(c.rec, n, sc.hist, before);
-      balanced_units_kernel<<<grid_for(P + 1, T), T, 0, s>>>(before, sc.dtot, n, P, SPM_ROW_COST,
-                                                            c.woff);
-      partitions_from_units_kernel<<<grid_for(p->kappa + 1, T), T, 0, s>>>(c.woff, p->kappa,
-                                                                          units, c.off);
-      continue;
-    }
     if (scheme != 1 || n == 0) {
-      equal_offsets_kernel<<<grid_for(p->kappa + 1, T), T, 0, s>>>(n, p->kappa, c.off);
-      units_from_partitions_kernel<<<grid_for(P + 1, T), T, 0, s>>>(c.off, p->kappa, units,
-                                                                    c.woff);
+      partition_copy<RI>(p, d, sc.hist, sc.dtot, reinterpret_cast<uint32_t*>(va), s);
       continue;
     }
     // Scheme 1: degree-ordered cyclic deal of the rows, copy ordered by partition.
@@ -783,6 +796,41 @@ spm_status build_copies_t(spmttkrp_plan_s* p, const int32_t* const* idx_in, cons
 }
 
 }  // namespace
+
+spm_status plan_repartition(spmttkrp_plan_s* p, int kappa, cudaStream_t s) {
+  if (kappa < 1 || kappa > 0xFFFF) return SPM_ERR_INVALID_ARG;
+  if (p->policy != (int)(SPM_POLICY_BALANCED >> 4) && p->policy != (int)(SPM_POLICY_SCHEME2 >> 4))
+    return SPM_ERR_UNSUPPORTED;
+  if (kappa == p->kappa) return SPM_OK;
+  if (kappa > p->kappa_cap) {
+    // the old arrays may still be read by queued work
+    SPM_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int d = 0; d < p->N; ++d) {
+      SPM_TRY(plan_realloc(p, (void**)&p->mode[d].off, sizeof(int64_t) * (size_t)(kappa + 1)));
+      SPM_TRY(plan_realloc(p, (void**)&p->mode[d].woff,
+                           sizeof(int64_t) * ((size_t)kappa * p->nu + 1)));
+    }
+    SPM_TRY(plan_realloc(p, (void**)&p->cta_part, sizeof(float) * 2 * (size_t)kappa * p->R));
+    SPM_TRY(plan_realloc(p, (void**)&p->cta_meta, sizeof(int) * 4 * (size_t)kappa));
+    p->kappa_cap = kappa;
+  }
+  p->kappa = kappa;
+  const int64_t n = p->nnz;
+  const int64_t nn = n > 0 ? n : 1;
+  uint32_t *hist = nullptr, *dtot = nullptr, *before = nullptr;
+  SPM_CUDA_TRY(cudaMallocAsync((void**)&hist, sizeof(uint32_t) * ceil_div<int64_t>(nn, RS_TILE), s));
+  SPM_CUDA_TRY(cudaMallocAsync((void**)&dtot, sizeof(uint32_t), s));
+  SPM_CUDA_TRY(cudaMallocAsync((void**)&before, sizeof(uint32_t) * nn, s));
+  for (int d = 0; d < p->N; ++d) {
+    if (record_int4s(p->N) == 1) partition_copy<1>(p, d, hist, dtot, before, s);
+    else partition_copy<2>(p, d, hist, dtot, before, s);
+  }
+  SPM_CUDA_TRY(cudaGetLastError());
+  SPM_CUDA_TRY(cudaFreeAsync(hist, s));
+  SPM_CUDA_TRY(cudaFreeAsync(dtot, s));
+  SPM_CUDA_TRY(cudaFreeAsync(before, s));
+  return SPM_OK;
+}
 
 spm_status build_copies(spmttkrp_plan_s* p, const int32_t* const* idx, const float* vals,
                         cudaStream_t s) {

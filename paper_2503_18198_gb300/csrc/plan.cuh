@@ -38,6 +38,7 @@ struct spmttkrp_plan_s {
   uint32_t flags = 0;
   bool bf16 = false;
   int kappa = 0;
+  int kappa_cap = 0;  // partitions the off/woff/cta arrays are sized for
   int nu = 0;      // work units per partition
   int policy = 0;  // SPM_POLICY_* >> 4
   spm_mode_copy mode[SPM_MAX_MODES];
@@ -52,6 +53,7 @@ struct spmttkrp_plan_s {
   size_t bytes = 0;
   // allocation bookkeeping
   void* allocs[64] = {};
+  size_t alloc_bytes[64] = {};
   int nallocs = 0;
 };
 
@@ -59,6 +61,13 @@ namespace spm {
 
 // Allocation owned by the plan (recorded for destroy and for plan_bytes).
 spm_status plan_alloc(spmttkrp_plan_s* p, void** ptr, size_t bytes);
+
+// Replace an allocation made by plan_alloc with a new one of `bytes`
+// (contents not kept).
+spm_status plan_realloc(spmttkrp_plan_s* p, void** ptr, size_t bytes);
+
+// P2 again for a new partition count (cost-balanced and Scheme 2 policies).
+spm_status plan_repartition(spmttkrp_plan_s* p, int kappa, cudaStream_t s);
 
 // P1 + P2: build every mode copy and its partition (plan.cu).
 spm_status build_copies(spmttkrp_plan_s* p, const int32_t* const* idx,
@@ -71,6 +80,9 @@ spm_status run_mttkrp(spmttkrp_plan_s* p, int mode, const void* const* factors,
 // P6: one CP-ALS sweep (als.cu).
 spm_status als_sweep(spmttkrp_plan_s* p, void* const* factors, double* lambda,
                      double* fit, cudaStream_t s);
+
+// G = Y^T Y (FP64, R x R) of a stored factor with the plan's block split (als.cu).
+spm_status gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, cudaStream_t s);
 
 // Allocate the plan's CP-ALS workspace on first use (als.cu).
 spm_status ensure_als_state(spmttkrp_plan_s* p);

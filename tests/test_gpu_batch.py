@@ -205,3 +205,30 @@ def test_batch_rejects_unsupported_mixes():
     assert e.value.status == 7
     with pytest.raises(spm.SpmError):
         spm.spm_batch_create([p32], [f32], lam, fits, max_sweeps=0)
+
+
+def test_autotune_then_batch_matches_single_tensor_sweeps():
+    """The autotuner times each candidate nonzeros-per-partition value and
+    leaves the plans partitioned for the fastest; batched sweeps on the tuned
+    plans equal single-tensor sweeps on the same plans bitwise."""
+    plans, facs, singles = [], [], []
+    for dims, nnz, R, seed in MIX:
+        plan, _, _ = make_plan(dims, nnz, R, seed)
+        plans.append(plan)
+        facs.append(init_factors(dims, R, seed, torch.float32))
+    cands = (0, 512, 4096, 1 << 15)
+    chosen, ms = spm.spm_batch_autotune(plans, facs, cands, reps=2)
+    assert chosen in cands
+    assert all(m > 0 for m in ms)
+    for t, (dims, nnz, R, seed) in enumerate(MIX):
+        k = spm.spm_device_sm_count() if chosen == 0 else max(1, -(-plans[t].nnz // chosen))
+        off = torch.empty(k + 1, dtype=torch.int64, device="cuda")
+        assert spm.spmttkrp_plan_partition(plans[t], 0, off) == k
+        fs = init_factors(dims, R, seed, torch.float32)
+        lam, fit = single_run(plans[t], fs, 2)
+        singles.append((fs, lam, fit))
+    B, _, _ = batch_run(plans, facs, 2)
+    for t, (fs, lam, fit) in enumerate(singles):
+        for w in range(len(fs)):
+            assert_same(facs[t][w], fs[w])
+        assert torch.equal(B.lam(t), lam)

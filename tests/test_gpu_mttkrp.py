@@ -243,3 +243,36 @@ def test_plan_bytes_counts_copies():
     plan = spm.spmttkrp_plan(dims, didx, dvals, R)
     b = spm.spmttkrp_plan_bytes(plan)
     assert b >= 3 * 4096 * (16 + 4)   # three 16-byte record copies + permutations
+
+
+@pytest.mark.parametrize("policy,flag", [("balanced", 0), ("scheme2", spm.SPM_POLICY_SCHEME2)])
+def test_repartition_keeps_copies_and_matches_oracle(policy, flag):
+    """P2 re-run for new partition counts (smaller, larger than the plan was
+    built with, and back): partitions bit-exact against the oracle's rule,
+    MTTKRP within tolerance for every mode."""
+    dims = (300, 120, 77)
+    _, idx, vals = synth.coo_random(dims, 25000, seed=21)
+    Y = synth.factors(dims, 32, seed=22)
+    plan, _, dfac = run_all_modes(dims, idx, vals, Y, flags=flag | spm.SPM_KAPPA(16))
+    for k in (3, 200, 1, 16, 1000):
+        spm.spmttkrp_plan_repartition(plan, k)
+        check_copies(plan, idx, kappa=k, policy=policy)
+        for d in range(3):
+            out = torch.full((dims[d], 32), float("nan"), device="cuda")
+            spm.spmttkrp_run(plan, d, dfac, out)
+            assert rel(out.cpu().numpy(), oracle.mttkrp(dims, idx, vals, Y, d)) < TOL
+    assert spm.spmttkrp_plan_status(plan) == 0
+
+
+def test_repartition_rejects_scheme1_and_bad_counts():
+    dims = (50, 40, 30)
+    _, idx, vals = synth.coo_random(dims, 2000, seed=3)
+    Y = synth.factors(dims, 16, seed=3)
+    p1, _, _ = run_all_modes(dims, idx, vals, Y, flags=spm.SPM_POLICY_SCHEME1)
+    with pytest.raises(spm.SpmError) as e:
+        spm.spmttkrp_plan_repartition(p1, 8)
+    assert e.value.status == 7
+    p0, _, _ = run_all_modes(dims, idx, vals, Y)
+    with pytest.raises(spm.SpmError) as e:
+        spm.spmttkrp_plan_repartition(p0, 70000)
+    assert e.value.status == 1
