@@ -49,6 +49,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="scale",
+                    choices=["scale", "batching", "serving", "precision"],
+                    help="scale (default, the headline line); the others print their "
+                         "own JSON line")
+    ap.add_argument("--tensors", type=int, default=512, help="batching: tensor count")
+    ap.add_argument("--sweeps", type=int, default=20, help="batching/precision: ALS sweeps")
+    ap.add_argument("--requests", type=int, default=200, help="serving: request count")
     return ap.parse_args()
 
 
@@ -235,6 +242,14 @@ def main():
     import synth
     import paper_2503_18198_gb300 as spm
     spm.load()  # fails loudly if the CUDA library is missing
+    if args.workload != "scale":
+        if rank == 0:  # the extra workloads run on one GPU
+            {"batching": run_batching, "serving": run_serving,
+             "precision": run_precision}[args.workload](args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
 
     dims, idx, vals, R, Y = synth.preset_torch("scale", nnz=args.nnz, device="cuda")
     N = len(dims)
@@ -382,6 +397,145 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def distinct_counts(idx):
+    import torch
+    return [int(torch.unique(c).numel()) for c in idx]
+
+
+def run_batching(args, rank, world):
+    """Batching workload: many small 3-mode tensors, 20 CP-ALS sweeps each.
+
+    Arms (same tensors, same initial factors):
+      * batched FP32 and batched BF16: spm_batch_autotune picks the
+        nonzeros per partition, then one CUDA graph of a whole batched sweep
+        (persistent per-class spMTTKRP launches fed by the (tensor,
+        partition) work queue, batched ALS passes) is replayed `sweeps` times;
+      * plain per-tensor FP32: cpd_als_step on each tensor in turn.
+    solves/s = tensors / time of all their sweeps (inputs resident in HBM,
+    plans built before timing).  The final fits of the BF16 batch are
+    compared with the plain FP32 path's (agreement within 1e-3)."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2503_18198_gb300 as spm
+    specs = synth.batching_specs(args.tensors)
+    S = args.sweeps
+    tens = []
+    for dims, nnz, R, seed in specs:
+        dims, idx, vals = synth.tensor_torch(dims, nnz, seed, device="cuda")
+        tens.append((dims, idx, vals, R, seed, distinct_counts(idx)))
+    n = len(tens)
+    total_nnz = sum(int(t[2].numel()) for t in tens)
+    stream = torch.cuda.current_stream()
+
+    def build(flags):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plans = [spm.spmttkrp_plan(d, i, v, R, flags) for d, i, v, R, _, _ in tens]
+        torch.cuda.synchronize()
+        return plans, (time.perf_counter() - t0) * 1e3
+
+    def factors(dtype):
+        return [[f.to(dtype).contiguous() for f in synth.factors_torch(d, R, seed, device="cuda")]
+                for d, _, _, R, seed, _ in tens]
+
+    def mttkrp_bytes(s_f):
+        return sum(sum(algorithmic_bytes(d, int(v.numel()), R, u, s_f))
+                   for d, _, v, R, _, u in tens)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    out = {}
+    cands = (0, 1 << 11, 1 << 13, 1 << 15, 1 << 17)
+    for name, flags, dtype, s_f in (("fp32_batched", spm.SPM_FACTOR_FP32, torch.float32, 4),
+                                    ("bf16_batched", spm.SPM_FACTOR_BF16, torch.bfloat16, 2)):
+        plans, plan_ms = build(flags)
+        facs = factors(dtype)
+        chosen, cms = spm.spm_batch_autotune(plans, facs, cands, reps=3)
+        lam = torch.zeros(sum(t[3] for t in tens), dtype=torch.float64, device="cuda")
+        fits = torch.zeros(n, dtype=torch.float64, device="cuda")
+        B = spm.spm_batch_create(plans, facs, lam, fits, tol=0.0, max_sweeps=S)
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream()
+        cs.wait_stream(stream)
+        with torch.cuda.stream(cs):
+            with torch.cuda.graph(g, stream=cs):
+                spm.spm_batch_sweep(B)
+        stream.wait_stream(cs)
+        ms = timed(lambda: [g.replay() for _ in range(S)])
+        active, nsw = spm.spm_batch_status(B)
+        assert all(x == S for x in nsw), nsw
+        assert all(spm.spmttkrp_plan_status(p) == 0 for p in plans)
+        best = cands.index(chosen)
+        out[name] = {"solves_per_s": n / (ms * 1e-3), "ms_total": ms, "ms_per_sweep": ms / S,
+                     "plan_build_ms": plan_ms,
+                     "autotune": {"nnz_per_partition_candidates": list(cands),
+                                  "mttkrp_all_modes_ms": [round(x, 4) for x in cms],
+                                  "chosen": chosen},
+                     "mttkrp_GBs": mttkrp_bytes(s_f) / (cms[best] * 1e-3) / 1e9,
+                     "mttkrp_all_modes_ms": cms[best],
+                     "launches_per_sweep_graph": "one graph"}
+        out[name]["fits"] = fits.cpu().numpy()
+        del g
+        B.destroy()
+        for p in plans:
+            p.destroy()
+        del facs
+    # plain per-tensor FP32 path
+    plans, plan_ms = build(spm.SPM_FACTOR_FP32)
+    facs = factors(torch.float32)
+    lams = [torch.zeros(t[3], dtype=torch.float64, device="cuda") for t in tens]
+    fits = torch.zeros(n, dtype=torch.float64, device="cuda")
+
+    def plain():
+        for t in range(n):
+            for _ in range(S):
+                spm.cpd_als_step(plans[t], facs[t], lams[t], fits[t:t + 1])
+    ms = timed(plain)
+    assert all(spm.spmttkrp_plan_status(p) == 0 for p in plans)
+    out["fp32_per_tensor"] = {"solves_per_s": n / (ms * 1e-3), "ms_total": ms,
+                              "plan_build_ms": plan_ms, "fits": fits.cpu().numpy()}
+    clk = clocks.stop()
+    ref = out["fp32_per_tensor"]["fits"]
+    agree = {}
+    for name in ("fp32_batched", "bf16_batched"):
+        dfit = np.abs(out[name].pop("fits") - ref)
+        agree[name + "_vs_fp32_per_tensor"] = {
+            "max_abs_dfit": float(dfit.max()), "within_1e-3": int((dfit <= 1e-3).sum()),
+            "of": n}
+    out["fp32_per_tensor"].pop("fits")
+    line = {
+        "workload": "batching", "metric": "CPD solves/s", "unit": "solves/s",
+        "value": out["bf16_batched"]["solves_per_s"], "higher_is_better": True,
+        "n_gpus": 1, "data": "synthetic",
+        "config": {"tensors": n, "total_nnz": total_nnz, "sweeps": S, "modes": 3,
+                   "ranks": "16 or 32", "dims": "log-uniform [100, 20000]",
+                   "nnz": "log-uniform [1e3, 2e6], at most half the cells",
+                   "l2": "inputs (mode copies of all tensors) larger than L2"},
+        "arms": out, "fit_agreement": agree,
+        "speedup_bf16_batched_vs_fp32_per_tensor":
+            out["bf16_batched"]["solves_per_s"] / out["fp32_per_tensor"]["solves_per_s"],
+        "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args, rank, world):
+    raise SystemExit("serving workload not built yet")
+
+
+def run_precision(args, rank, world):
+    raise SystemExit("precision workload not built yet")
 
 
 def plan_kappa(spm, plan):

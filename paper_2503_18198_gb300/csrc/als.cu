@@ -78,7 +78,7 @@ template <typename FT>
 spm_status launch_gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, cudaStream_t s) {
   const int R = p->R;
   spm_als_state& A = p->als;
-  const int nb = work_blocks(I, GRAM_TILE_ROWS, A.gram_blocks);
+  const int nb = als_row_blocks(I, A.gram_blocks);
   const int64_t rpb = ceil_div<int64_t>(I, nb);
   const FT* y = static_cast<const FT*>(Y);
   switch (gram_tile(R)) {
@@ -142,12 +142,12 @@ spm_status als_sweep(spmttkrp_plan_s* p, void* const* factors, double* lambda, d
     const int64_t I = p->dims[d];
     SPM_TRY(run_mttkrp(p, d, factors, A.M, s));
     system_kernel<<<1, ALS_THREADS, 0, s>>>(A.gram, N, d, R, A.chol, A.winv, p->dev_err);
-    const int nb = work_blocks(I, 4 * (ALS_THREADS / 32), nb_solve);
+    const int nb = als_row_blocks(I, nb_solve);
     if (R <= 32) solve_kernel<1><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err);
     else solve_kernel<2><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err);
     lambda_kernel<<<1, 256, 0, s>>>(A.colsq_part, nb, R, A.lambda_ws, p->dev_err);
     const bool last = d == N - 1;
-    const int nbs = work_blocks(I, ALS_THREADS / R, nb_solve);
+    const int nbs = als_row_blocks(I, nb_solve);
     if (p->bf16)
       scale_kernel<__nv_bfloat16><<<nbs, ALS_THREADS, 0, s>>>(
           A.Z, A.lambda_ws, I, R, static_cast<__nv_bfloat16*>(factors[d]), last ? A.M : nullptr,

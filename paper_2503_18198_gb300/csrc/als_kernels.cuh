@@ -15,6 +15,10 @@ namespace spm {
 
 constexpr int ALS_THREADS = 256;
 constexpr int GRAM_TILE_ROWS = 32;
+// Fewest rows a virtual block of a row pass takes: per-block partials (R x R
+// for the Gram, R for the column sums) and the per-block load of V^{-1} are
+// then small next to the rows themselves.
+constexpr int ALS_MIN_ROWS = 256;
 
 // ---- double-float helpers (Dekker / Knuth error-free transformations) ----
 struct df {
@@ -205,9 +209,12 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ M,
                                            const int* __restrict__ err, int vb, int nvb) {
   constexpr int ROWS = 4;
   __shared__ double red[ALS_THREADS / 32][32 * RPL];
+  __shared__ float2 w_s[(32 * RPL) * (32 * RPL)];  // V^{-1} as (hi, lo) pairs
   if (*err) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int RR = R * R;
+  for (int e = threadIdx.x; e < RR; e += ALS_THREADS) w_s[e] = make_float2(winv[e], winv[RR + e]);
+  __syncthreads();
   const int64_t gwarp = (int64_t)vb * (ALS_THREADS / 32) + warp;
   const int64_t nwarps = (int64_t)nvb * (ALS_THREADS / 32);
   df sq[RPL];
@@ -219,17 +226,31 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ M,
     for (int q = 0; q < ROWS; ++q)
 #pragma unroll
       for (int j = 0; j < RPL; ++j) acc[q][j] = {0.f, 0.f};
-    for (int s = 0; s < R; ++s) {
-      float m[ROWS];
+    // lane l holds M(i0 + q, l + 32 c); broadcast by shuffles below
+    float mrow[ROWS][RPL];
 #pragma unroll
-      for (int q = 0; q < ROWS; ++q) m[q] = (i0 + q < I) ? M[(i0 + q) * R + s] : 0.f;
+    for (int q = 0; q < ROWS; ++q)
 #pragma unroll
-      for (int j = 0; j < RPL; ++j) {
-        const int r = lane + 32 * j;
-        if (r < R) {
-          const float wh = winv[s * R + r], wl = winv[RR + s * R + r];
+      for (int c = 0; c < RPL; ++c) {
+        const int s = lane + 32 * c;
+        mrow[q][c] = (i0 + q < I && s < R) ? M[(i0 + q) * R + s] : 0.f;
+      }
 #pragma unroll
-          for (int q = 0; q < ROWS; ++q) df_add_prod2(acc[q][j], m[q], wh, wl);
+    for (int c = 0; c < RPL; ++c) {
+      const int send = min(32, R - 32 * c);
+      for (int sl = 0; sl < send; ++sl) {
+        const int s = 32 * c + sl;
+        float m[ROWS];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) m[q] = __shfl_sync(SPM_FULL_MASK, mrow[q][c], sl);
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+          const int r = lane + 32 * j;
+          if (r < R) {
+            const float2 w = w_s[s * R + r];
+#pragma unroll
+            for (int q = 0; q < ROWS; ++q) df_add_prod2(acc[q][j], m[q], w.x, w.y);
+          }
         }
       }
     }
@@ -363,5 +384,10 @@ __host__ __device__ inline int gram_tile(int R) { return R <= 16 ? 1 : R <= 32 ?
 inline int work_blocks(int64_t I, int64_t rows_per_block_min, int cap) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(cap, ceil_div<int64_t>(I, rows_per_block_min)));
 }
+
+// The block split of every row pass of a mode with I rows (Gram partials,
+// solve, scale).  A function of I and the plan's cap only, so that a tensor's
+// sums are grouped the same way alone and in a batch.
+inline int als_row_blocks(int64_t I, int cap) { return work_blocks(I, ALS_MIN_ROWS, cap); }
 
 }  // namespace spm

@@ -204,10 +204,10 @@ spm_status batch_add(spm_batch_s* B, spmttkrp_plan_s* p, void* const* factors, d
     a.nin = p->N - 1;
     a.nu = p->nu;
     // the single-tensor sweep's virtual block counts (identical sums)
-    b.nb_gram[d] = work_blocks(I, GRAM_TILE_ROWS, A.gram_blocks);
+    b.nb_gram[d] = als_row_blocks(I, A.gram_blocks);
     b.gram_rpb[d] = ceil_div<int64_t>(I, b.nb_gram[d]);
-    b.nb_solve[d] = work_blocks(I, 4 * (ALS_THREADS / 32), A.gram_blocks);
-    b.nb_scale[d] = work_blocks(I, ALS_THREADS / p->R, A.gram_blocks);
+    b.nb_solve[d] = als_row_blocks(I, A.gram_blocks);
+    b.nb_scale[d] = als_row_blocks(I, A.gram_blocks);
   }
   for (int w = 0; w < p->N; ++w)
     SPM_TRY(gram(p, factors[w], p->dims[w], A.gram + (size_t)w * p->R * p->R, s));

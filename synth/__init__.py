@@ -19,6 +19,15 @@ available here:
                  uniform, 100M distinct coordinates, values lognormal(0,1),
                  R = 64.
 
+* ``batching``   512 independent 3-mode tensors, each dim log-uniform in
+                 [100, 20,000], nnz log-uniform in [1e3, 2e6] (at most half
+                 the cells, so that distinct coordinates can be drawn),
+                 uniform coordinates, values U(0,1), R drawn from {16, 32}.
+* ``serving``    a Poisson stream (mean 200 requests/s) of CP-ALS jobs, 3 or
+                 4 modes, dims log-uniform in [1e3, 1e6], nnz log-uniform in
+                 [1e4, 5e7], Zipf(1.1) coordinates, values U(0,1), R drawn
+                 from {8, 16, 32, 64}.
+
 A COO tensor is returned as ``(dims, idx, vals)`` with ``idx`` a list of
 int32 arrays (one per mode) and ``vals`` float32.
 """
@@ -125,7 +134,7 @@ def coo_distinct(dims, nnz, alphas=None, seed=0, values="uniform",
 
 
 def coo_distinct_torch(dims, nnz, alphas=None, seed=0, values="uniform",
-                       device="cpu", oversample=2.4):
+                       device="cpu", oversample=2.4, max_rounds=None):
     """The recipe of :func:`coo_distinct` drawn with torch on `device`.
 
     Used for the large workloads (tens of millions of nonzeros, where the
@@ -134,6 +143,8 @@ def coo_distinct_torch(dims, nnz, alphas=None, seed=0, values="uniform",
     deduplicated together keeping first occurrences, and the first `nnz`
     survivors in draw order are kept.  The random stream differs from the
     numpy one, so the two functions give different (equally valid) tensors.
+    With `max_rounds` the drawing stops after that many rounds and fewer
+    than `nnz` nonzeros may be returned (heavily skewed small shapes).
     Returns (dims, idx list of int32 tensors, vals float32 tensor)."""
     import torch
     dims = tuple(int(d) for d in dims)
@@ -156,7 +167,9 @@ def coo_distinct_torch(dims, nnz, alphas=None, seed=0, values="uniform",
     strides = strides[::-1]
     cand = [torch.empty(0, dtype=torch.int32, device=device) for _ in dims]
     draw = int(nnz * oversample) + 1024
+    rounds = 0
     while True:
+        rounds += 1
         for w, (n, c) in enumerate(zip(dims, cdfs)):
             if c is None:
                 x = torch.randint(0, n, (draw,), generator=g, device=device,
@@ -176,6 +189,9 @@ def coo_distinct_torch(dims, nnz, alphas=None, seed=0, values="uniform",
         del lin, srt, order, head
         if first.numel() >= nnz:
             first = first[:nnz]
+            break
+        if max_rounds is not None and rounds >= max_rounds:
+            nnz = int(first.numel())
             break
         draw = int((nnz - first.numel()) * oversample * 2) + 4096
     idx = [cand[w][first].contiguous() for w in range(N)]
@@ -265,3 +281,48 @@ def rank_r_blocks(dims, rank, block, seed=0):
             vals.append(v)
     idx = [np.asarray(a, dtype=np.int32) for a in idx]
     return tuple(int(d) for d in dims), idx, np.asarray(vals), true
+
+
+def _log_uniform(g: np.random.Generator, lo: float, hi: float) -> float:
+    return float(np.exp(g.uniform(np.log(lo), np.log(hi))))
+
+
+def batching_specs(count: int = 512, seed: int = 4):
+    """The batching workload: a list of (dims, nnz, rank, seed) per tensor."""
+    g = rng(seed)
+    out = []
+    for t in range(count):
+        dims = tuple(int(round(_log_uniform(g, 100, 20_000))) for _ in range(3))
+        nnz = int(round(_log_uniform(g, 1e3, 2e6)))
+        cells = int(np.prod(np.asarray(dims, dtype=np.float64)))
+        nnz = max(1, min(nnz, cells // 2))
+        rank = int(g.choice([16, 32]))
+        out.append((dims, nnz, rank, seed * 1_000_000 + t))
+    return out
+
+
+def serving_specs(count: int, rate: float = 200.0, seed: int = 5):
+    """The serving workload: a list of (arrival_s, dims, nnz, rank, seed)
+    with Poisson arrivals of mean `rate` per second."""
+    g = rng(seed)
+    t = 0.0
+    out = []
+    for j in range(count):
+        t += float(g.exponential(1.0 / rate))
+        N = int(g.choice([3, 4]))
+        dims = tuple(int(round(_log_uniform(g, 1e3, 1e6))) for _ in range(N))
+        nnz = int(round(_log_uniform(g, 1e4, 5e7)))
+        rank = int(g.choice([8, 16, 32, 64]))
+        out.append((t, dims, nnz, rank, seed * 1_000_000 + j))
+    return out
+
+
+SERVING_ALPHA = 1.1
+
+
+def tensor_torch(dims, nnz, seed, alpha=None, device="cpu", max_rounds=None):
+    """One tensor of the batching (alpha None: uniform) or serving (Zipf
+    alpha on every mode) workloads, drawn on `device`."""
+    alphas = None if alpha is None else (alpha,) * len(dims)
+    return coo_distinct_torch(dims, nnz, alphas, seed=seed, values="uniform",
+                              device=device, max_rounds=max_rounds)
