@@ -247,6 +247,15 @@ spm_status spmttkrp_run_noalloc(int nmodes, const int64_t *dims, int64_t nnz,
 spm_status cpd_als_step(spmttkrp_plan_t plan, void *const *factors,
                         double *lambda, double *fit, void *stream);
 
+/* Device bytes a plan of this shape holds once cpd_als_step has run on it
+ * (*resident: mode copies, partitions, MTTKRP and CP-ALS workspace; equals
+ * spmttkrp_plan_bytes of such a plan) and the most its build adds for a while
+ * on top (*transient, may be NULL: the sort scratch).  Factors, lambda and
+ * fit buffers are the caller's and not included.  Host only. */
+spm_status spmttkrp_plan_bytes_estimate(int nmodes, const int64_t *dims, int64_t nnz,
+                                        int rank, uint32_t flags, size_t *resident,
+                                        size_t *transient);
+
 /* Re-run P2 (Sec. III-B) for a new partition count kappa (0 = the SM count,
  * else 1..65535); the mode copies are kept.  Only for the BALANCED and
  * SCHEME2 policies (else SPM_ERR_UNSUPPORTED).  Growing kappa beyond the
@@ -312,6 +321,78 @@ spm_status spm_batch_autotune(int ntensors, const spmttkrp_plan_t *plans,
                               void *const *factors, const int64_t *candidates,
                               int ncandidates, int reps, int64_t *chosen,
                               float *ms, void *stream);
+
+/* ---- serving: continuous batching of CP-ALS jobs ------------------------------ */
+
+/* A server runs CP-ALS jobs (Sec. II-A5 as cpd_als_step, until the fit changes
+ * by less than the job's tolerance or its sweep limit) on the current device.
+ * The caller drives it with spm_server_step in a loop: each step launches one
+ * batched sweep of every running job (as spm_batch_sweep), admits queued jobs
+ * in arrival order while the running-job limit and the device-memory budget
+ * allow (building their plans on a second stream, overlapping the sweep),
+ * then retires the jobs that stopped.  A job's result is bitwise the one
+ * cpd_als_step gives on a plan with the same flags, whatever else runs.
+ * The paper has no serving layer; this is the GPU-resident job loop around
+ * its MTTKRP. */
+typedef struct spm_server_s *spm_server_t;
+
+enum { SPM_JOB_QUEUED = 0, SPM_JOB_RUNNING = 1, SPM_JOB_DONE = 2, SPM_JOB_FAILED = 3 };
+
+typedef struct {
+  int nmodes;                  /* 3 or 4                                     */
+  const int64_t *dims;         /* host [nmodes]                              */
+  int64_t nnz;
+  const int32_t *const *idx;   /* host array of nmodes device pointers [nnz] */
+  const float *vals;           /* device [nnz]                               */
+  int rank;                    /* 8, 16, 32 or 64                            */
+  const float *const *init;    /* host array of nmodes device pointers to the
+                                  initial FP32 factors I_w x R (16-byte
+                                  aligned; rounded to BF16 for BF16 servers) */
+  double tol;                  /* stop when |fit change| < tol               */
+  int max_sweeps;              /* ... or after this many sweeps (>= 1)       */
+} spm_job_desc;
+
+typedef struct {
+  int state;                   /* SPM_JOB_*                                  */
+  spm_status status;           /* why, when SPM_JOB_FAILED                   */
+  int sweeps;                  /* sweeps run (when done)                     */
+  double fit;                  /* final fit (when done)                      */
+  size_t bytes;                /* device bytes the job holds now             */
+  size_t est_bytes;            /* its admission estimate (plan + factors)    */
+  double queued_ms;            /* submit -> admission (host clock)           */
+  double total_ms;             /* submit -> retirement: time to solution     */
+} spm_job_info;
+
+/* hbm_budget: device bytes the server's jobs may hold at once (plans,
+ * factors, and the transient sort scratch of a build); max_active: running
+ * jobs at most; flags: SPM_FACTOR_FP32 or SPM_FACTOR_BF16;
+ * nnz_per_partition: partitions per job = ceil(nnz / this), 1..65535
+ * (0 = one per SM). */
+spm_status spm_server_create(spm_server_t *out, size_t hbm_budget, int max_active,
+                             uint32_t flags, int64_t nnz_per_partition);
+
+/* Queue a job; *job receives its id.  The inputs (idx, vals, init) must be
+ * complete on the device (their producing stream synchronised) and stay valid
+ * until the job has left SPM_JOB_QUEUED.  A job whose estimate exceeds the
+ * budget fails with SPM_ERR_OOM at its turn. */
+spm_status spm_server_submit(spm_server_t server, const spm_job_desc *desc, int64_t *job);
+
+/* One step (sweep, admission, retirement); synchronises the server's streams.
+ * *running / *queued (may be NULL) receive the counts after the step. */
+spm_status spm_server_step(spm_server_t server, int *running, int *queued);
+
+spm_status spm_server_job(spm_server_t server, int64_t job, spm_job_info *info);
+
+/* Copy a finished job's factors (stored type, device, NULL entries skipped)
+ * and weights (device double[R], may be NULL) out on `stream`, synchronise,
+ * and release the job.  Returns the failure status for a failed job. */
+spm_status spm_server_result(spm_server_t server, int64_t job, void *const *factors,
+                             double *lambda, void *stream);
+
+/* Device bytes held by the server's jobs now, and the budget. */
+spm_status spm_server_usage(spm_server_t server, size_t *used, size_t *budget);
+
+void spm_server_destroy(spm_server_t server);
 
 /* Synchronise `stream` and return the plan's sticky device-side error
  * (SPM_OK, SPM_ERR_NUMERIC or SPM_ERR_TIMEOUT), then clear it. */

@@ -51,7 +51,10 @@ SYMBOLS = ("spmttkrp_plan", "spmttkrp_plan_bytes", "spmttkrp_plan_permutation",
            "spmttkrp_plan_destroy", "spmttkrp_run", "cpd_als_step",
            "spmttkrp_plan_status", "spm_status_string", "spm_device_sm_count",
            "spmttkrp_run_noalloc", "spmttkrp_plan_repartition", "spm_batch_create", "spm_batch_sweep",
-           "spm_batch_status", "spm_batch_destroy", "spm_batch_autotune")
+           "spm_batch_status", "spm_batch_destroy", "spm_batch_autotune",
+           "spmttkrp_plan_bytes_estimate", "spm_server_create", "spm_server_submit",
+           "spm_server_step", "spm_server_job", "spm_server_result", "spm_server_usage",
+           "spm_server_destroy")
 
 
 def library_path() -> str:
@@ -107,6 +110,22 @@ def load(build_if_missing: bool = False):
     lib.spm_batch_status.restype = i32
     lib.spm_batch_autotune.argtypes = [i32, P, P, P, i32, i32, P, P, P]
     lib.spm_batch_autotune.restype = i32
+    lib.spmttkrp_plan_bytes_estimate.argtypes = [i32, P, i64, i32, u32, P, P]
+    lib.spmttkrp_plan_bytes_estimate.restype = i32
+    lib.spm_server_create.argtypes = [P, ctypes.c_size_t, i32, u32, i64]
+    lib.spm_server_create.restype = i32
+    lib.spm_server_submit.argtypes = [P, P, P]
+    lib.spm_server_submit.restype = i32
+    lib.spm_server_step.argtypes = [P, P, P]
+    lib.spm_server_step.restype = i32
+    lib.spm_server_job.argtypes = [P, i64, P]
+    lib.spm_server_job.restype = i32
+    lib.spm_server_result.argtypes = [P, i64, P, P, P]
+    lib.spm_server_result.restype = i32
+    lib.spm_server_usage.argtypes = [P, P, P]
+    lib.spm_server_usage.restype = i32
+    lib.spm_server_destroy.argtypes = [P]
+    lib.spm_server_destroy.restype = None
     lib.spm_batch_destroy.argtypes = [P]
     lib.spm_batch_destroy.restype = None
     lib.spm_device_sm_count.argtypes = []
@@ -363,3 +382,115 @@ def spm_batch_autotune(plans, factors, candidates=(0, 1 << 12, 1 << 14, 1 << 16,
                                      ctypes.byref(chosen), ms, _stream(stream)),
            "spm_batch_autotune")
     return int(chosen.value), list(ms)
+
+
+def spmttkrp_plan_bytes_estimate(dims, nnz: int, rank: int, flags: int = 0):
+    """(resident, transient) device bytes of a plan of this shape (host only)."""
+    N = len(dims)
+    dims_a = (ctypes.c_int64 * N)(*[int(d) for d in dims])
+    res, tr = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load().spmttkrp_plan_bytes_estimate(N, dims_a, int(nnz), int(rank),
+                                               int(flags) & 0xFFFFFFFF, ctypes.byref(res),
+                                               ctypes.byref(tr)),
+           "spmttkrp_plan_bytes_estimate")
+    return int(res.value), int(tr.value)
+
+
+SPM_JOB_QUEUED, SPM_JOB_RUNNING, SPM_JOB_DONE, SPM_JOB_FAILED = 0, 1, 2, 3
+
+
+class JobDesc(ctypes.Structure):
+    _fields_ = [("nmodes", ctypes.c_int), ("dims", ctypes.c_void_p), ("nnz", ctypes.c_int64),
+                ("idx", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("rank", ctypes.c_int),
+                ("init", ctypes.c_void_p), ("tol", ctypes.c_double),
+                ("max_sweeps", ctypes.c_int)]
+
+
+class JobInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("sweeps", ctypes.c_int),
+                ("fit", ctypes.c_double), ("bytes", ctypes.c_size_t),
+                ("est_bytes", ctypes.c_size_t), ("queued_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
+
+
+class Server:
+    """Owns an spm_server_t (continuous batching of CP-ALS jobs).  Keeps the
+    submitted input tensors alive until their jobs are admitted."""
+
+    def __init__(self, budget_bytes: int, max_active: int = 64, flags: int = 0,
+                 nnz_per_partition: int = 1 << 17):
+        h = ctypes.c_void_p()
+        _check(load().spm_server_create(ctypes.byref(h), int(budget_bytes), int(max_active),
+                                        int(flags), int(nnz_per_partition)),
+               "spm_server_create")
+        self.handle = h
+        self.flags = int(flags)
+        self._inputs = {}
+        self.ranks = {}
+        self.shapes = {}
+
+    def submit(self, dims, idx, vals, rank: int, init, tol: float = 1e-4,
+               max_sweeps: int = 50) -> int:
+        """idx: N int32 CUDA tensors, vals float32 CUDA, init: N float32 CUDA
+        [I_w, R].  The producing stream must be synchronised first."""
+        N = len(dims)
+        dims_a = (ctypes.c_int64 * N)(*[int(d) for d in dims])
+        idx_a = (ctypes.c_void_p * N)(*[c.data_ptr() for c in idx])
+        init_a = (ctypes.c_void_p * N)(*[f.data_ptr() for f in init])
+        nnz = int(vals.numel())
+        d = JobDesc(N, ctypes.cast(dims_a, ctypes.c_void_p).value, nnz,
+                    ctypes.cast(idx_a, ctypes.c_void_p).value if nnz else None,
+                    vals.data_ptr() if nnz else None, int(rank),
+                    ctypes.cast(init_a, ctypes.c_void_p).value, float(tol), int(max_sweeps))
+        job = ctypes.c_int64()
+        _check(load().spm_server_submit(self.handle, ctypes.byref(d), ctypes.byref(job)),
+               "spm_server_submit")
+        j = int(job.value)
+        self._inputs[j] = (idx, vals, init)
+        self.ranks[j] = int(rank)
+        self.shapes[j] = tuple(int(x) for x in dims)
+        return j
+
+    def step(self):
+        """One step; returns (running, queued)."""
+        r, q = ctypes.c_int(), ctypes.c_int()
+        _check(load().spm_server_step(self.handle, ctypes.byref(r), ctypes.byref(q)),
+               "spm_server_step")
+        for j in list(self._inputs):
+            if self.info(j).state != SPM_JOB_QUEUED:
+                del self._inputs[j]
+        return int(r.value), int(q.value)
+
+    def info(self, job: int) -> JobInfo:
+        i = JobInfo()
+        _check(load().spm_server_job(self.handle, int(job), ctypes.byref(i)), "spm_server_job")
+        return i
+
+    def result(self, job: int, stream=None):
+        """(factors, lambda) of a finished job as new CUDA tensors; releases it."""
+        import torch
+        dt = torch.bfloat16 if self.flags & SPM_FACTOR_BF16 else torch.float32
+        R = self.ranks[job]
+        fac = [torch.empty(n, R, dtype=dt, device="cuda") for n in self.shapes[job]]
+        lam = torch.empty(R, dtype=torch.float64, device="cuda")
+        _check(load().spm_server_result(self.handle, int(job), _ptrs(fac),
+                                        ctypes.c_void_p(lam.data_ptr()), _stream(stream)),
+               "spm_server_result")
+        return fac, lam
+
+    def usage(self):
+        u, b = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(load().spm_server_usage(self.handle, ctypes.byref(u), ctypes.byref(b)),
+               "spm_server_usage")
+        return int(u.value), int(b.value)
+
+    def destroy(self):
+        if self.handle:
+            load().spm_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

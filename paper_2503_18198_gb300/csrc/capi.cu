@@ -192,6 +192,19 @@ spm_status spmttkrp_plan_scheme(spmttkrp_plan_t plan, int mode, int* scheme) {
   return SPM_OK;
 }
 
+spm_status spmttkrp_plan_bytes_estimate(int nmodes, const int64_t* dims, int64_t nnz, int rank,
+                                        uint32_t flags, size_t* resident, size_t* transient) {
+  if (nmodes < 2 || nmodes > SPM_MAX_MODES || !dims || nnz < 0 || rank < 1 ||
+      rank > SPM_MAX_RANK || !resident)
+    return SPM_ERR_INVALID_ARG;
+  int kappa = (int)SPM_KAPPA_OF(flags);
+  if (kappa == 0) kappa = sm_count();
+  size_t tr = 0;
+  plan_bytes_estimate(nmodes, dims, nnz, rank, kappa, true, resident, &tr);
+  if (transient) *transient = tr;
+  return SPM_OK;
+}
+
 spm_status spmttkrp_plan_repartition(spmttkrp_plan_t plan, int kappa, void* stream) {
   if (!plan) return SPM_ERR_INVALID_ARG;
   if (kappa == 0) kappa = sm_count();

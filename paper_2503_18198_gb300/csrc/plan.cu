@@ -797,6 +797,41 @@ spm_status build_copies_t(spmttkrp_plan_s* p, const int32_t* const* idx_in, cons
 
 }  // namespace
 
+void plan_bytes_estimate(int N, const int64_t* dims, int64_t nnz, int R, int kappa, bool als,
+                         size_t* resident, size_t* transient) {
+  // mirrors the plan_alloc calls of spmttkrp_plan, build_copies and
+  // ensure_als_state (each allocation of 0 bytes counts 16)
+  const int RI = record_int4s(N);
+  const int nu = SPM_UNITS_PER_PARTITION(R);
+  const int64_t nn = nnz > 0 ? nnz : 1;
+  int64_t Imax = 1;
+  for (int w = 0; w < N; ++w) Imax = std::max(Imax, dims[w]);
+  size_t b = sizeof(int) + sizeof(double);  // dev_err, normX2
+  b += sizeof(float) * 2 * (size_t)kappa * R + sizeof(int) * 4 * (size_t)kappa;
+  b += sizeof(double) * NORM_BLOCKS;
+  for (int d = 0; d < N; ++d) {
+    b += sizeof(int4) * RI * (size_t)nn + 256;
+    b += sizeof(int32_t) * (size_t)nn;
+    b += sizeof(int64_t) * (size_t)(kappa + 1);
+    b += sizeof(int64_t) * ((size_t)kappa * nu + 1);
+    b += sizeof(uint32_t) * (size_t)((dims[d] + 31) / 32);
+  }
+  if (als) {
+    const size_t gb = (size_t)std::max(1, sm_count()) * 4;
+    const size_t RR = (size_t)R * R;
+    b += sizeof(double) * RR * N + sizeof(double) * RR * gb + sizeof(double) * RR;
+    b += sizeof(float) * 2 * RR + sizeof(double) * R * gb * 2 + sizeof(double) * R;
+    b += sizeof(float) * (size_t)Imax * R * 2;
+  }
+  *resident = b;
+  // stream-ordered scratch of the build (keys, payloads, histograms)
+  const int64_t cap = std::max(nn, Imax);
+  *transient = sizeof(unsigned long long) * 2 * (size_t)cap + sizeof(int32_t) * 2 * (size_t)cap +
+               sizeof(uint32_t) * RS_BINS * (size_t)ceil_div<int64_t>(cap, RS_TILE) +
+               sizeof(uint32_t) * RS_BINS + sizeof(int64_t) * SPM_MAX_MODES +
+               sizeof(unsigned long long) * SPM_MAX_MODES;
+}
+
 spm_status plan_repartition(spmttkrp_plan_s* p, int kappa, cudaStream_t s) {
   if (kappa < 1 || kappa > 0xFFFF) return SPM_ERR_INVALID_ARG;
   if (p->policy != (int)(SPM_POLICY_BALANCED >> 4) && p->policy != (int)(SPM_POLICY_SCHEME2 >> 4))

@@ -66,6 +66,12 @@ spm_status plan_alloc(spmttkrp_plan_s* p, void** ptr, size_t bytes);
 // (contents not kept).
 spm_status plan_realloc(spmttkrp_plan_s* p, void** ptr, size_t bytes);
 
+// Device bytes a plan holds (resident: copies, partitions, workspace, and
+// with `als` the CP-ALS state) and the most its build adds for a while
+// (transient scratch), for the given shape.
+void plan_bytes_estimate(int N, const int64_t* dims, int64_t nnz, int R, int kappa, bool als,
+                         size_t* resident, size_t* transient);
+
 // P2 again for a new partition count (cost-balanced and Scheme 2 policies).
 spm_status plan_repartition(spmttkrp_plan_s* p, int kappa, cudaStream_t s);
 
