@@ -246,7 +246,7 @@ spm_status batch_commit(spm_batch_s* B, cudaStream_t s) {
     for (int d = 0; d < p->N; ++d) B->host[t].margs[d].woff = p->mode[d].woff;
     const int kc = B->host[t].kclass;
     B->mtt_smem[kc] =
-        std::max(B->mtt_smem[kc], mttkrp_smem_bytes(p->R, record_int4s(p->N), p->nu));
+        std::max(B->mtt_smem[kc], mttkrp_smem_bytes(p->R, record_int4s(p->N), p->nu, p->bf16 ? 2 : 4));
   }
   std::vector<int2>& v = B->stage;
   v.clear();

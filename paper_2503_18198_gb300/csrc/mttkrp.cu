@@ -87,7 +87,7 @@ spm_status run_mttkrp(spmttkrp_plan_s* p, int mode, const void* const* factors, 
     SPM_CUDA_TRY(cudaGetLastError());
   }
   MttkrpKernelFn fn = pick_mttkrp(p->bf16, p->N - 1, R);
-  const size_t smem = mttkrp_smem_bytes(R, record_int4s(p->N), p->nu);
+  const size_t smem = mttkrp_smem_bytes(R, record_int4s(p->N), p->nu, p->bf16 ? 2 : 4);
   SPM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // Smallest shared-memory carve-out that fits: the rest of the unified
   // array is L1 for the gathered factor rows.

@@ -124,7 +124,7 @@ extern "C" spm_status spmttkrp_run_noalloc(int nmodes, const int64_t* dims, int6
   a.nu = nu;
   a.err = err;  // a bounded-wait timeout flag lands here; this entry does not read it
   MttkrpKernelFn fn = pick_mttkrp(bf16, nmodes - 1, rank);
-  const size_t smem = mttkrp_smem_bytes(rank, record_int4s(nmodes), nu);
+  const size_t smem = mttkrp_smem_bytes(rank, record_int4s(nmodes), nu, bf16 ? 2 : 4);
   SPM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   fn<<<kappa, MT_THREADS, smem, s>>>(a);
   SPM_CUDA_TRY(cudaGetLastError());

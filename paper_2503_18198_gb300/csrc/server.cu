@@ -243,6 +243,10 @@ spm_status spm_server_step(spm_server_t S, int* running, int* queued) {
   std::vector<Job*> admitted;
   while (!S->queue.empty() &&
          (int)(S->running.size() + admitted.size()) < S->max_active) {
+    // once the sweep is over, further builds would only keep it waiting:
+    // the rest join at a later step
+    if (!admitted.empty() && !S->running.empty() && cudaStreamQuery(S->s_sweep) == cudaSuccess)
+      break;
     Job* j = S->queue.front();
     const size_t need = j->resident + factor_bytes(S, j);
     if (need + j->transient > S->budget) {  // can never fit
