@@ -96,9 +96,13 @@ typedef enum {
   ((4096 / (R)) < 16 ? 16 : ((4096 / (R)) > 128 ? 128 : (4096 / (R))))
 #define SPM_ROW_COST 16 /* extra cost of a row start, in nonzeros */
 
-/* Number of partitions kappa.  0 (default) = the device's SM count, one
- * thread block per SM (Sec. III-B: one partition per streaming
- * multiprocessor).  Any value 1..65535 may be forced, e.g. for tests. */
+/* Number of partitions kappa.  0 (default) = SPM_PARTITIONS_PER_SM times the
+ * device's SM count.  The paper assigns one partition per streaming
+ * multiprocessor (Sec. III-B); on GB300 two resident waves of partition
+ * blocks per SM balance the per-partition time variance (the block
+ * scheduler gives a free SM the next partition).  Any value 1..65535 may be
+ * forced, e.g. SPM_KAPPA(sm count) for the paper's one-per-SM layout. */
+#define SPM_PARTITIONS_PER_SM 2
 #define SPM_KAPPA(k) (((uint32_t)(k) & 0xFFFFu) << 16)
 #define SPM_KAPPA_OF(flags) (((uint32_t)(flags) >> 16) & 0xFFFFu)
 
@@ -256,7 +260,7 @@ spm_status spmttkrp_plan_bytes_estimate(int nmodes, const int64_t *dims, int64_t
                                         int rank, uint32_t flags, size_t *resident,
                                         size_t *transient);
 
-/* Re-run P2 (Sec. III-B) for a new partition count kappa (0 = the SM count,
+/* Re-run P2 (Sec. III-B) for a new partition count kappa (0 = the default of SPM_KAPPA(0),
  * else 1..65535); the mode copies are kept.  Only for the BALANCED and
  * SCHEME2 policies (else SPM_ERR_UNSUPPORTED).  Growing kappa beyond the
  * largest value the plan has had synchronises `stream` and reallocates the
@@ -310,7 +314,7 @@ void spm_batch_destroy(spm_batch_t batch);
 
 /* Autotuner of the batched spMTTKRP: picks the nonzeros per partition.  For
  * each candidate c (c > 0: every tensor gets kappa = ceil(nnz / c) partitions,
- * at most 65535; c == 0: one per SM) the plans are repartitioned
+ * at most 65535; c == 0: the plan default, SPM_KAPPA(0)) the plans are repartitioned
  * (spmttkrp_plan_repartition) and the batched spMTTKRP of all modes is timed
  * with CUDA events on `stream`, the best of `reps` runs after one warm-up.
  * The plans are left partitioned for the fastest candidate (*chosen);
@@ -367,7 +371,7 @@ typedef struct {
  * factors, and the transient sort scratch of a build); max_active: running
  * jobs at most; flags: SPM_FACTOR_FP32 or SPM_FACTOR_BF16;
  * nnz_per_partition: partitions per job = ceil(nnz / this), 1..65535
- * (0 = one per SM). */
+ * (0 = the plan default, SPM_KAPPA(0)). */
 spm_status spm_server_create(spm_server_t *out, size_t hbm_budget, int max_active,
                              uint32_t flags, int64_t nnz_per_partition);
 

@@ -33,6 +33,14 @@ SPM_MAX_MODES = 7
 SPM_MAX_RANK = 256
 
 
+SPM_PARTITIONS_PER_SM = 2
+
+
+def default_kappa() -> int:
+    """Partition count of a plan made with SPM_KAPPA(0)."""
+    return SPM_PARTITIONS_PER_SM * spm_device_sm_count()
+
+
 def SPM_KAPPA(k: int) -> int:
     return (int(k) & 0xFFFF) << 16
 

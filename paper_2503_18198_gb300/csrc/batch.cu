@@ -436,9 +436,8 @@ spm_status spm_batch_autotune(int ntensors, const spmttkrp_plan_t* plans, void* 
   for (int c = 0; c < ncandidates; ++c)
     if (candidates[c] < 0) return SPM_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int sms = std::max(1, sm_count());
   auto kappa_for = [&](const spmttkrp_plan_s* p, int64_t target) -> int {
-    if (target == 0) return sms;
+    if (target == 0) return default_kappa();
     return (int)std::max<int64_t>(1, std::min<int64_t>(0xFFFF, ceil_div<int64_t>(p->nnz, target)));
   };
   // scratch weights and fits for the timing batches

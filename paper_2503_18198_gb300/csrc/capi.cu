@@ -56,6 +56,11 @@ int sm_count() {
   return n;
 }
 
+int default_kappa() {
+  const int n = sm_count();
+  return n < 1 ? n : SPM_PARTITIONS_PER_SM * n;
+}
+
 namespace {
 
 void free_plan(spmttkrp_plan_s* p) {
@@ -115,7 +120,7 @@ spm_status spmttkrp_plan(spmttkrp_plan_t* out, int nmodes, const int64_t* dims, 
   const int policy = (int)((flags & SPM_POLICY_MASK) >> 4);
   if (policy > 3) return SPM_ERR_INVALID_ARG;
   int kappa = (int)SPM_KAPPA_OF(flags);
-  if (kappa == 0) kappa = sm_count();
+  if (kappa == 0) kappa = default_kappa();
   if (kappa < 1) return SPM_ERR_CUDA;
 
   spmttkrp_plan_s* p = new (std::nothrow) spmttkrp_plan_s();
@@ -198,7 +203,7 @@ spm_status spmttkrp_plan_bytes_estimate(int nmodes, const int64_t* dims, int64_t
       rank > SPM_MAX_RANK || !resident)
     return SPM_ERR_INVALID_ARG;
   int kappa = (int)SPM_KAPPA_OF(flags);
-  if (kappa == 0) kappa = sm_count();
+  if (kappa == 0) kappa = default_kappa();
   size_t tr = 0;
   plan_bytes_estimate(nmodes, dims, nnz, rank, kappa, true, resident, &tr);
   if (transient) *transient = tr;
@@ -207,7 +212,7 @@ spm_status spmttkrp_plan_bytes_estimate(int nmodes, const int64_t* dims, int64_t
 
 spm_status spmttkrp_plan_repartition(spmttkrp_plan_t plan, int kappa, void* stream) {
   if (!plan) return SPM_ERR_INVALID_ARG;
-  if (kappa == 0) kappa = sm_count();
+  if (kappa == 0) kappa = default_kappa();
   return plan_repartition(plan, kappa, static_cast<cudaStream_t>(stream));
 }
 

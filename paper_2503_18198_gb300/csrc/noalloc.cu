@@ -79,7 +79,7 @@ extern "C" spm_status spmttkrp_run_noalloc(int nmodes, const int64_t* dims, int6
       (records && (reinterpret_cast<uintptr_t>(records) & 15u)))
     return SPM_ERR_INVALID_ARG;
   int kappa = (int)SPM_KAPPA_OF(flags);
-  if (kappa == 0) kappa = sm_count();
+  if (kappa == 0) kappa = default_kappa();
   if (kappa < 1) return SPM_ERR_CUDA;
   const int nu = SPM_UNITS_PER_PARTITION(rank);
   const int64_t P = (int64_t)kappa * nu;

@@ -95,4 +95,8 @@ spm_status ensure_als_state(spmttkrp_plan_s* p);
 
 int sm_count();
 
+// Partition count of a plan made with SPM_KAPPA(0): SPM_PARTITIONS_PER_SM
+// per SM (-1 when the device cannot be queried).
+int default_kappa();
+
 }  // namespace spm

@@ -72,7 +72,6 @@ struct spm_server_s {
   int max_active = 0;
   uint32_t flags = 0;   // factor type
   int64_t nnz_per_partition = 0;
-  int sms = 1;
   cudaStream_t s_sweep = nullptr;
   cudaStream_t s_build = nullptr;
   spm_batch_s* B = nullptr;
@@ -179,7 +178,6 @@ spm_status spm_server_create(spm_server_t* out, size_t hbm_budget, int max_activ
   S->max_active = max_active;
   S->flags = flags;
   S->nnz_per_partition = nnz_per_partition;
-  S->sms = std::max(1, sm_count());
   S->B = new (std::nothrow) spm_batch_s();
   if (!S->B || cudaStreamCreateWithFlags(&S->s_sweep, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&S->s_build, cudaStreamNonBlocking) != cudaSuccess) {
@@ -219,7 +217,7 @@ spm_status spm_server_submit(spm_server_t S, const spm_job_desc* d, int64_t* job
   }
   j->tol = d->tol;
   j->max_sweeps = d->max_sweeps;
-  int kappa = S->sms;
+  int kappa = default_kappa();
   if (S->nnz_per_partition > 0)
     kappa = (int)std::max<int64_t>(
         1, std::min<int64_t>(0xFFFF, ceil_div<int64_t>(std::max<int64_t>(1, d->nnz),

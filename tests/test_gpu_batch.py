@@ -221,7 +221,7 @@ def test_autotune_then_batch_matches_single_tensor_sweeps():
     assert chosen in cands
     assert all(m > 0 for m in ms)
     for t, (dims, nnz, R, seed) in enumerate(MIX):
-        k = spm.spm_device_sm_count() if chosen == 0 else max(1, -(-plans[t].nnz // chosen))
+        k = spm.binding.default_kappa() if chosen == 0 else max(1, -(-plans[t].nnz // chosen))
         off = torch.empty(k + 1, dtype=torch.int64, device="cuda")
         assert spm.spmttkrp_plan_partition(plans[t], 0, off) == k
         fs = init_factors(dims, R, seed, torch.float32)

@@ -79,7 +79,7 @@ def run_fullsize(name, dtype, flags, check_structure):
     idx_h = [c.cpu().numpy() for c in idx]
     vals_h = vals.cpu().numpy()
     fac_h = [f.float().cpu().numpy() for f in fac]   # the factors the GPU used
-    kappa = spm.spm_device_sm_count()
+    kappa = spm.binding.default_kappa()
     U = spm.SPM_UNITS_PER_PARTITION(R)
     rng = np.random.default_rng(7)
     for d in range(N):

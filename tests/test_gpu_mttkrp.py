@@ -65,7 +65,7 @@ def check_copies(plan, idx, kappa=None, policy="balanced"):
         spm.spmttkrp_plan_permutation(plan, d, perm)
         ref = oracle.mode_permutation(idx, d)
         assert np.array_equal(perm.cpu().numpy(), ref), f"mode {d} permutation"
-        k = kappa or spm.spm_device_sm_count()
+        k = kappa or spm.binding.default_kappa()
         off = torch.empty(k + 1, dtype=torch.int64, device="cuda")
         assert spm.spmttkrp_plan_partition(plan, d, off) == k
         units = torch.empty(k * U + 1, dtype=torch.int64, device="cuda")
