@@ -309,7 +309,8 @@ def main():
         try:
             with open(tfile) as f:
                 tj = json.load(f)
-            if tj.get("nnz") == nnz:
+            # counters taken on this workload with the current kernel sources only
+            if tj.get("nnz") == nnz and tj.get("kernel_digest") == kernel_digest():
                 traffic = tj.get("bytes_per_launch")
         except (OSError, ValueError):
             traffic = None
@@ -648,6 +649,20 @@ def run_serving(args, rank, world):
 
 def run_precision(args, rank, world):
     raise SystemExit("precision workload not built yet")
+
+
+KERNEL_SOURCES = ("mttkrp_kernel.cuh", "mttkrp.cu", "mttkrp_inst.cuh", "common.cuh", "plan.cuh")
+
+
+def kernel_digest():
+    """sha256 over the MTTKRP kernel's sources (ties stored ncu counters to
+    the code they were taken on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2503_18198_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def plan_kappa(spm, plan):
