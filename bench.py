@@ -648,7 +648,119 @@ def run_serving(args, rank, world):
 
 
 def run_precision(args, rank, world):
-    raise SystemExit("precision workload not built yet")
+    """Precision workload: 4-mode 20,000 x 20,000 x 5,000 x 24 COO, 100M
+    nonzeros (Zipf(1.0) x3 + uniform, lognormal values), R = 64, factors
+    stored in FP32 or BF16 with FP32 accumulation; Gram/Cholesky in FP64.
+
+    Reports per arm: spMTTKRP time and algorithmic GB/s per mode (inputs
+    resident, larger than L2), the error of sampled output rows against the
+    FP64 oracle (BF16: against the oracle on the same BF16-rounded factors --
+    the accumulation error -- and on the FP32 factors -- the total error),
+    and `sweeps` CP-ALS sweeps from the same initial factors (time per sweep,
+    final fit, and the BF16 - FP32 fit difference)."""
+    import numpy as np
+    import torch
+    import oracle
+    import synth
+    import paper_2503_18198_gb300 as spm
+    dims, idx, vals, R, Y = synth.preset_torch("precision", device="cuda")
+    N = len(dims)
+    nnz = int(vals.numel())
+    distinct = distinct_counts(idx)
+    idx_h = [c.cpu().numpy() for c in idx]
+    vals_h = vals.cpu().numpy()
+    Y_h = [y.cpu().numpy() for y in Y]
+    Yb_h = [oracle.store_round(y, "bf16") for y in Y_h]
+    rng = np.random.default_rng(7)
+    rows = []
+    for d in range(N):
+        deg = np.bincount(idx_h[d], minlength=dims[d])
+        heavy = np.argsort(-deg, kind="stable")[:4]
+        nz = np.nonzero(deg)[0]
+        rows.append(np.unique(np.concatenate([heavy, rng.choice(nz, min(96, nz.size), replace=False)]))
+                    .astype(np.int32))
+    ref32 = [oracle.mttkrp_rows(dims, idx_h, vals_h, Y_h, d, rows[d]) for d in range(N)]
+    ref16 = [oracle.mttkrp_rows(dims, idx_h, vals_h, Yb_h, d, rows[d]) for d in range(N)]
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    peak, peak_kind = measured_peak()
+    arms = {}
+    fits = {}
+    for name, flags, dtype, s_f in (("fp32", spm.SPM_FACTOR_FP32, torch.float32, 4),
+                                    ("bf16", spm.SPM_FACTOR_BF16, torch.bfloat16, 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan = spm.spmttkrp_plan(dims, idx, vals, R, flags)
+        torch.cuda.synchronize()
+        plan_ms = (time.perf_counter() - t0) * 1e3
+        fac = [y.to(dtype).clone() for y in Y]  # never alias the preset factors
+        outs = [torch.empty(dims[d], R, device="cuda") for d in range(N)]
+        B = algorithmic_bytes(dims, nnz, R, distinct, s_f)
+        ms = []
+        for d in range(N):
+            for _ in range(3):
+                spm.spmttkrp_run(plan, d, fac, outs[d])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(10):
+                spm.spmttkrp_run(plan, d, fac, outs[d])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1) / 10)
+        err = {}
+        for d in range(N):
+            got = outs[d][torch.as_tensor(rows[d]).long().cuda()].double().cpu().numpy()
+            if name == "fp32":
+                err[f"mode{d}"] = rel(got, ref32[d])
+            else:
+                err[f"mode{d}"] = {"vs_oracle_same_bf16_factors": rel(got, ref16[d]),
+                                   "vs_oracle_fp32_factors": rel(got, ref32[d])}
+        lam = torch.zeros(R, dtype=torch.float64, device="cuda")
+        fit = torch.zeros(1, dtype=torch.float64, device="cuda")
+        fac = [y.to(dtype).clone() for y in Y]  # never alias the preset factors
+        spm.cpd_als_step(plan, [f.clone() for f in fac], lam, fit)  # warm-up on a copy
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.sweeps):
+            spm.cpd_als_step(plan, fac, lam, fit)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        als_ms = e0.elapsed_time(e1) / args.sweeps
+        assert spm.spmttkrp_plan_status(plan) == 0
+        fits[name] = float(fit.item())
+        arms[name] = {
+            "plan_ms": plan_ms, "plan_bytes": spm.spmttkrp_plan_bytes(plan),
+            "mttkrp_ms_per_mode": [round(m, 4) for m in ms],
+            "mttkrp_GBs_per_mode": [round(b / (m * 1e-3) / 1e9, 1) for b, m in zip(B, ms)],
+            "roofline_frac_per_mode": [round(b / (m * 1e-3) / 1e9 / peak, 4) for b, m in zip(B, ms)],
+            "mttkrp_GBs_all_modes": sum(B) / (sum(ms) * 1e-3) / 1e9,
+            "nnz_per_s_per_mode": [round(nnz / (m * 1e-3), 1) for m in ms],
+            "algorithmic_bytes_per_mode": B,
+            "sampled_row_rel_error": err,
+            "als_ms_per_sweep": als_ms, "fit_after_sweeps": fits[name]}
+        plan.destroy()
+        del fac, outs
+    clk = clocks.stop()
+    line = {
+        "workload": "precision", "metric": "spMTTKRP GB/s per mode, FP32 vs BF16 factors",
+        "unit": "GB/s", "value": arms["bf16"]["mttkrp_GBs_all_modes"], "higher_is_better": True,
+        "n_gpus": 1, "data": "synthetic",
+        "config": {"dims": list(dims), "nnz": nnz, "rank": R, "sweeps": args.sweeps,
+                   "coords": "Zipf(1.0) x3 + uniform", "values": "lognormal(0,1)",
+                   "l2": "inputs larger than L2", "peak": peak, "peak_source": peak_kind,
+                   "sampled_rows_per_mode": [int(r.size) for r in rows]},
+        "arms": arms, "fit_bf16_minus_fp32": fits["bf16"] - fits["fp32"],
+        "bf16_speedup_mttkrp": arms["fp32"]["mttkrp_GBs_all_modes"] and
+            sum(arms["fp32"]["mttkrp_ms_per_mode"]) / sum(arms["bf16"]["mttkrp_ms_per_mode"]),
+        "clocks": clk}
+    print(json.dumps(line), flush=True)
 
 
 KERNEL_SOURCES = ("mttkrp_kernel.cuh", "mttkrp.cu", "mttkrp_inst.cuh", "common.cuh", "plan.cuh")

@@ -1,5 +1,5 @@
 """Parity at the full workload sizes, in the launch configuration bench.py
-times (default plan: cost-balanced work units, one partition per SM).
+times (default plan: cost-balanced work units, two partitions per SM).
 
 * scale: 1,000,000 x 500,000 x 200,000, 50M nonzeros, Zipf(1.2), R = 32 FP32.
 * precision: 20,000 x 20,000 x 5,000 x 24, 100M nonzeros, Zipf(1.0) x3 +
