@@ -148,6 +148,36 @@ __device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32
 }
 
 // 128-bit read-only load with an L2 cache policy.
+// Read-only 16-byte load with an L2 policy, schedulable like a plain load.
+__device__ __forceinline__ uint4 ld_nc_v4_pol(const void* p, uint64_t policy) {
+  uint4 r;
+  asm("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p), "l"(policy));
+  return r;
+}
+
+// Packed FP32 pairs (sm_100 and later): each lane of the pair is rounded
+// exactly as the scalar mul.rn / fma.rn.
+__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
 __device__ __forceinline__ uint4 ld_nc_v4_hint(const void* p, uint64_t policy) {
   uint4 r;
   asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"

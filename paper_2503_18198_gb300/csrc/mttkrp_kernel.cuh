@@ -83,6 +83,12 @@ enum : int {
   META_EMPTY = 16,
 };
 
+#ifndef SPM_MT_F32X2
+#define SPM_MT_F32X2 1  // 1: packed FP32-pair arithmetic in the full-step path
+#endif
+#ifndef SPM_MT_REUSE
+#define SPM_MT_REUSE 0  // 1: a slot keeps its first input mode's row and skips a repeated gather
+#endif
 #ifndef SPM_MT_CONTIG
 #define SPM_MT_CONTIG 0  // 1: slots stream contiguous sub-ranges of a unit
 #endif
@@ -606,6 +612,17 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
           // full steps (a record in every slot), U at a time
           const int nb = ((n / G) / U) * U;
           const unsigned char* rb = reinterpret_cast<const unsigned char*>(recs) + slot * 16 * RI;
+#if SPM_MT_REUSE
+          int last0 = -1;               // index of the first input mode's row held in y0prev
+          uint32_t y0prev[CPL][RAWN];
+#pragma unroll
+          for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int i = 0; i < RAWN; ++i) y0prev[c][i] = 0u;
+#endif
+#if SPM_L2_HINTS
+          const uint64_t pol_rows = l2_policy_evict_last();
+#endif
           for (int j = 0; j < nb; j += U) {
             int w[U][W];
             uint32_t y[U][NINF][CPL][RAWN];
@@ -617,17 +634,47 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
                 w[uu][4 * qq] = v4.x; w[uu][4 * qq + 1] = v4.y;
                 w[uu][4 * qq + 2] = v4.z; w[uu][4 * qq + 3] = v4.w;
               }
+#if SPM_MT_REUSE
+            bool fresh0[U];
+            {
+              int prev = last0;
+#pragma unroll
+              for (int uu = 0; uu < U; ++uu) {
+                fresh0[uu] = w[uu][1] != prev;
+                prev = w[uu][1];
+              }
+            }
+#endif
 #pragma unroll
             for (int uu = 0; uu < U; ++uu)
 #pragma unroll
               for (int m = 0; m < NINF; ++m)
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) {
-                  const uint4 x = __ldg(facb[m] + (size_t)(uint32_t)w[uu][1 + m] * (RT * sizeof(FT) / 16) +
-                                        c * LPN);
+#if SPM_MT_REUSE
+                  if (m == 0 && !fresh0[uu]) continue;  // taken from the previous step below
+#endif
+                  const uint4* src = facb[m] + (size_t)(uint32_t)w[uu][1 + m] * (RT * sizeof(FT) / 16) + c * LPN;
+#if SPM_L2_HINTS
+                  const uint4 x = ld_nc_v4_pol(src, pol_rows);
+#else
+                  const uint4 x = __ldg(src);
+#endif
                   y[uu][m][c][0] = x.x; y[uu][m][c][1] = x.y;
                   y[uu][m][c][2] = x.z; y[uu][m][c][3] = x.w;
                 }
+#if SPM_MT_REUSE
+#pragma unroll
+            for (int uu = 0; uu < U; ++uu)
+#pragma unroll
+              for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int i = 0; i < RAWN; ++i) {
+                  if (!fresh0[uu]) y[uu][0][c][i] = uu == 0 ? y0prev[c][i] : y[uu - 1][0][c][i];
+                  if (uu == U - 1) y0prev[c][i] = y[uu][0][c][i];
+                }
+            last0 = w[U - 1][1];
+#endif
             bool same = pure;
             if (!pure) {
               bool ok = true;
@@ -643,6 +690,39 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
               for (int c = 0; c < CPL; ++c) {
                 float f[VEC], g[VEC];
                 S::cvt(y[uu][0][c], f);
+#if SPM_MT_F32X2
+                // the same roundings as the scalar code, two ranks per instruction
+                const uint64_t vv = f2_pack(val, val);
+                uint64_t g2[VEC / 2];
+#pragma unroll
+                for (int e = 0; e < VEC / 2; ++e) g2[e] = f2_mul(vv, f2_pack(f[2 * e], f[2 * e + 1]));
+#pragma unroll
+                for (int m = 1; m + 1 < NINF; ++m) {
+                  S::cvt(y[uu][m][c], f);
+#pragma unroll
+                  for (int e = 0; e < VEC / 2; ++e) g2[e] = f2_mul(g2[e], f2_pack(f[2 * e], f[2 * e + 1]));
+                }
+                if (NINF > 1) S::cvt(y[uu][NINF - 1][c], f);
+#pragma unroll
+                for (int e = 0; e < VEC / 2; ++e) {
+                  const uint64_t fl = f2_pack(f[2 * e], f[2 * e + 1]);
+                  if (same) {
+                    uint64_t a2 = f2_pack(acc[c][2 * e], acc[c][2 * e + 1]);
+                    a2 = NINF > 1 ? f2_fma(g2[e], fl, a2) : f2_mul(g2[e], f2_pack(1.f, 1.f));
+                    if (NINF > 1) f2_unpack(a2, acc[c][2 * e], acc[c][2 * e + 1]);
+                    else {
+                      float g0, g1;
+                      f2_unpack(g2[e], g0, g1);
+                      acc[c][2 * e] += g0;
+                      acc[c][2 * e + 1] += g1;
+                    }
+                  } else {
+                    const uint64_t p2 = NINF > 1 ? f2_mul(g2[e], fl) : g2[e];
+                    f2_unpack(p2, v[c][2 * e], v[c][2 * e + 1]);
+                  }
+                }
+                (void)g;
+#else
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) g[e] = val * f[e];
 #pragma unroll
@@ -657,6 +737,7 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
                   if (same) acc[c][e] = NINF > 1 ? fmaf(g[e], f[e], acc[c][e]) : acc[c][e] + g[e];
                   else v[c][e] = NINF > 1 ? g[e] * f[e] : g[e];
                 }
+#endif
               }
               if (!same) step_rows(w[uu][0], v);
             }
