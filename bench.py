@@ -50,7 +50,7 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="scale",
-                    choices=["scale", "batching", "serving", "precision"],
+                    choices=["scale", "batching", "serving", "precision", "schemes"],
                     help="scale (default, the headline line); the others print their "
                          "own JSON line")
     ap.add_argument("--tensors", type=int, default=512, help="batching: tensor count")
@@ -251,8 +251,8 @@ def main():
     spm.load()  # fails loudly if the CUDA library is missing
     if args.workload != "scale":
         if rank == 0:  # the extra workloads run on one GPU
-            {"batching": run_batching, "serving": run_serving,
-             "precision": run_precision}[args.workload](args, rank, world)
+            {"batching": run_batching, "serving": run_serving, "precision": run_precision,
+             "schemes": run_schemes}[args.workload](args, rank, world)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
@@ -405,6 +405,79 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+SCHEME_SHAPES = [
+    # (name, dims, nnz, Zipf exponents (None = uniform), rank)
+    ("scale-20M", (1_000_000, 500_000, 200_000), 20_000_000, (1.2, 1.2, 1.2), 32),
+    ("precision-30M", (20_000, 20_000, 5_000, 24), 30_000_000, (1.0, 1.0, 1.0, None), 64),
+    ("uniform-20M", (100_000, 100_000, 100_000), 20_000_000, (None, None, None), 32),
+    ("short-modes-20M", (200_000, 5_000, 64), 20_000_000, (1.1, 1.1, None), 32),
+]
+
+
+def run_schemes(args, rank, world):
+    """The paper's load-balancing ablation (Sec. III-B): spMTTKRP time per
+    mode under Scheme 1 only, Scheme 2 only and the adaptive rule (Scheme 1
+    when I_d >= kappa), all at the paper's kappa = SM count, plus this
+    build's default (cost-balanced work units, two partitions per SM).
+    Reports geometric-mean speedups over all (shape, mode) pairs."""
+    import math
+    import torch
+    import synth
+    import paper_2503_18198_gb300 as spm
+    sms = spm.spm_device_sm_count()
+    pols = [("scheme1", spm.SPM_POLICY_SCHEME1 | spm.SPM_KAPPA(sms)),
+            ("scheme2", spm.SPM_POLICY_SCHEME2 | spm.SPM_KAPPA(sms)),
+            ("adaptive", spm.SPM_POLICY_ADAPTIVE | spm.SPM_KAPPA(sms)),
+            ("balanced_1_per_sm", spm.SPM_POLICY_BALANCED | spm.SPM_KAPPA(sms)),
+            ("balanced_default", spm.SPM_POLICY_BALANCED),
+            ("balanced_autotuned", spm.SPM_POLICY_BALANCED)]
+    stream = torch.cuda.current_stream()
+    res = {}
+    for si, (name, dims, nnz, alphas, R) in enumerate(SCHEME_SHAPES):
+        dims, idx, vals = synth.coo_distinct_torch(dims, nnz, alphas, seed=40 + si, device="cuda")
+        Y = synth.factors_torch(dims, R, seed=40 + si, device="cuda")
+        outs = [torch.empty(dims[d], R, device="cuda") for d in range(len(dims))]
+        res[name] = {}
+        for pname, flags in pols:
+            plan = spm.spmttkrp_plan(dims, idx, vals, R, flags)
+            if pname == "balanced_autotuned":
+                spm.spmttkrp_plan_autotune(plan, Y)
+            ms = []
+            for d in range(len(dims)):
+                for _ in range(2):
+                    spm.spmttkrp_run(plan, d, Y, outs[d])
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(5):
+                    spm.spmttkrp_run(plan, d, Y, outs[d])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(round(e0.elapsed_time(e1) / 5, 4))
+            res[name][pname] = {"ms_per_mode": ms,
+                                "scheme_per_mode": [spm.spmttkrp_plan_scheme(plan, d)
+                                                    for d in range(len(dims))]}
+            plan.destroy()
+        del idx, vals, Y, outs
+
+    def geomean(a, b):
+        logs = [math.log(x / y) for n in res for x, y in
+                zip(res[n][a]["ms_per_mode"], res[n][b]["ms_per_mode"])]
+        return math.exp(sum(logs) / len(logs))
+    line = {"workload": "schemes", "metric": "spMTTKRP ms per mode by partitioning policy",
+            "unit": "ms", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"kappa_paper": sms, "shapes": [s[0] for s in SCHEME_SHAPES],
+                       "factors": "fp32"},
+            "results": res,
+            "geomean_speedup": {
+                "adaptive_over_scheme1": geomean("scheme1", "adaptive"),
+                "adaptive_over_scheme2": geomean("scheme2", "adaptive"),
+                "balanced_1_per_sm_over_adaptive": geomean("adaptive", "balanced_1_per_sm"),
+                "balanced_default_over_adaptive": geomean("adaptive", "balanced_default"),
+                "balanced_autotuned_over_adaptive": geomean("adaptive", "balanced_autotuned")}}
+    print(json.dumps(line), flush=True)
 
 
 def distinct_counts(idx):
@@ -706,6 +779,7 @@ def run_precision(args, rank, world):
         torch.cuda.synchronize()
         plan_ms = (time.perf_counter() - t0) * 1e3
         fac = [y.to(dtype).clone() for y in Y]  # never alias the preset factors
+        kappa, kappa_ms = spm.spmttkrp_plan_autotune(plan, fac)  # 1 or 2 partitions per SM
         outs = [torch.empty(dims[d], R, device="cuda") for d in range(N)]
         B = algorithmic_bytes(dims, nnz, R, distinct, s_f)
         ms = []
@@ -744,6 +818,7 @@ def run_precision(args, rank, world):
         fits[name] = float(fit.item())
         arms[name] = {
             "plan_ms": plan_ms, "plan_bytes": spm.spmttkrp_plan_bytes(plan),
+            "kappa_autotuned": kappa, "kappa_candidates_ms_all_modes": [round(x, 4) for x in kappa_ms],
             "mttkrp_ms_per_mode": [round(m, 4) for m in ms],
             "mttkrp_GBs_per_mode": [round(b / (m * 1e-3) / 1e9, 1) for b, m in zip(B, ms)],
             "roofline_frac_per_mode": [round(b / (m * 1e-3) / 1e9 / peak, 4) for b, m in zip(B, ms)],

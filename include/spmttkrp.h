@@ -268,6 +268,20 @@ spm_status spmttkrp_plan_bytes_estimate(int nmodes, const int64_t *dims, int64_t
  * FP32 summation order.  Must not be called while a batch holds the plan. */
 spm_status spmttkrp_plan_repartition(spmttkrp_plan_t plan, int kappa, void *stream);
 
+/* Autotune the partition count of one plan: for each candidate kappa
+ * (kappas[0..nkappas-1]; NULL = {SM count, 2 x SM count}) the plan is
+ * repartitioned and spmttkrp_run of every mode is timed with CUDA events on
+ * `stream` (best of `reps` after one warm-up, outputs written to the plan's
+ * CP-ALS workspace, which is allocated if absent).  The plan is left at the
+ * fastest candidate, *chosen receives it and ms[c] (host, may be NULL) each
+ * candidate's time for all modes.  Factors as for spmttkrp_run (read only).
+ * BALANCED and SCHEME2 policies only.  Synchronises `stream`.  The paper fixes
+ * one partition per SM (Sec. III-B); which count is fastest on GB300 depends
+ * on the tensor's skew, hence the measurement. */
+spm_status spmttkrp_plan_autotune(spmttkrp_plan_t plan, const void *const *factors,
+                                  const int *kappas, int nkappas, int reps, int *chosen,
+                                  float *ms, void *stream);
+
 /* ---- batched CP-ALS over many tensors ---------------------------------------- */
 
 /* A batch runs CP-ALS sweeps (Sec. II-A5, as cpd_als_step) over many independent

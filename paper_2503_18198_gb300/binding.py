@@ -58,7 +58,8 @@ SYMBOLS = ("spmttkrp_plan", "spmttkrp_plan_bytes", "spmttkrp_plan_permutation",
            "spmttkrp_plan_partition", "spmttkrp_plan_work_units", "spmttkrp_plan_scheme",
            "spmttkrp_plan_destroy", "spmttkrp_run", "cpd_als_step",
            "spmttkrp_plan_status", "spm_status_string", "spm_device_sm_count",
-           "spmttkrp_run_noalloc", "spmttkrp_plan_repartition", "spm_batch_create", "spm_batch_sweep",
+           "spmttkrp_run_noalloc", "spmttkrp_plan_repartition", "spmttkrp_plan_autotune",
+           "spm_batch_create", "spm_batch_sweep",
            "spm_batch_status", "spm_batch_destroy", "spm_batch_autotune",
            "spmttkrp_plan_bytes_estimate", "spm_server_create", "spm_server_submit",
            "spm_server_step", "spm_server_job", "spm_server_result", "spm_server_usage",
@@ -108,6 +109,8 @@ def load(build_if_missing: bool = False):
     lib.spm_status_string.restype = ctypes.c_char_p
     lib.spmttkrp_run_noalloc.argtypes = [i32, P, i64, i32, i32, P, P, u32, P, P]
     lib.spmttkrp_run_noalloc.restype = i32
+    lib.spmttkrp_plan_autotune.argtypes = [P, P, P, i32, i32, P, P, P]
+    lib.spmttkrp_plan_autotune.restype = i32
     lib.spmttkrp_plan_repartition.argtypes = [P, i32, P]
     lib.spmttkrp_plan_repartition.restype = i32
     lib.spm_batch_create.argtypes = [P, i32, P, P, P, P, ctypes.c_double, i32, P]
@@ -254,6 +257,20 @@ def spmttkrp_plan_repartition(plan: Plan, kappa: int, stream=None):
     """Recompute the partitions for kappa partitions (0 = SM count)."""
     _check(load().spmttkrp_plan_repartition(plan.handle, int(kappa), _stream(stream)),
            "spmttkrp_plan_repartition")
+
+
+def spmttkrp_plan_autotune(plan: Plan, factors, kappas=None, reps: int = 3, stream=None):
+    """Time candidate partition counts (default: 1 and 2 per SM) on the given
+    factors and leave the plan at the fastest; returns (chosen, ms list)."""
+    n = len(kappas) if kappas else 2
+    ka = (ctypes.c_int * n)(*[int(k) for k in kappas]) if kappas else None
+    ms = (ctypes.c_float * n)()
+    chosen = ctypes.c_int()
+    _check(load().spmttkrp_plan_autotune(plan.handle, _ptrs(list(factors)), ka,
+                                         n if kappas else 0, int(reps), ctypes.byref(chosen),
+                                         ms, _stream(stream)),
+           "spmttkrp_plan_autotune")
+    return int(chosen.value), list(ms)
 
 
 def spmttkrp_plan_destroy(plan: Plan):

@@ -216,6 +216,63 @@ spm_status spmttkrp_plan_repartition(spmttkrp_plan_t plan, int kappa, void* stre
   return plan_repartition(plan, kappa, static_cast<cudaStream_t>(stream));
 }
 
+spm_status spmttkrp_plan_autotune(spmttkrp_plan_t plan, const void* const* factors,
+                                  const int* kappas, int nkappas, int reps, int* chosen,
+                                  float* ms, void* stream) {
+  if (!plan || !factors || reps < 1 || (kappas && nkappas < 1) || !chosen) return SPM_ERR_INVALID_ARG;
+  if (plan->policy != (int)(SPM_POLICY_BALANCED >> 4) && plan->policy != (int)(SPM_POLICY_SCHEME2 >> 4))
+    return SPM_ERR_UNSUPPORTED;
+  const int sms = sm_count();
+  if (sms < 1) return SPM_ERR_CUDA;
+  const int dflt[2] = {sms, 2 * sms};
+  if (!kappas) {
+    kappas = dflt;
+    nkappas = 2;
+  }
+  for (int c = 0; c < nkappas; ++c)
+    if (kappas[c] < 1 || kappas[c] > 0xFFFF) return SPM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  SPM_TRY(ensure_als_state(plan));  // its M buffer (I_max x R) takes the outputs
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return SPM_ERR_CUDA;
+  }
+  spm_status st = SPM_OK;
+  int best = -1;
+  float best_ms = 0.f;
+  for (int c = 0; c < nkappas && st == SPM_OK; ++c) {
+    st = plan_repartition(plan, kappas[c], s);
+    float t_min = 0.f;
+    for (int r = 0; r <= reps && st == SPM_OK; ++r) {  // r == 0 warms up
+      cudaEventRecord(e0, s);
+      for (int d = 0; d < plan->N && st == SPM_OK; ++d)
+        st = run_mttkrp(plan, d, factors, plan->als.M, s);
+      cudaEventRecord(e1, s);
+      if (st == SPM_OK && cudaEventSynchronize(e1) != cudaSuccess) st = SPM_ERR_CUDA;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r == 1 || (r > 1 && t < t_min)) t_min = t;
+    }
+    if (st != SPM_OK) break;
+    if (ms) ms[c] = t_min;
+    if (best < 0 || t_min < best_ms) {
+      best = c;
+      best_ms = t_min;
+    }
+  }
+  if (st == SPM_OK) {
+    st = plan_repartition(plan, kappas[best], s);
+    *chosen = kappas[best];
+  }
+  if (st == SPM_OK && cudaStreamSynchronize(s) != cudaSuccess) st = SPM_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  (void)cudaGetLastError();
+  return st;
+}
+
 void spmttkrp_plan_destroy(spmttkrp_plan_t plan) {
   if (!plan) return;
   cudaDeviceSynchronize();

@@ -276,3 +276,21 @@ def test_repartition_rejects_scheme1_and_bad_counts():
     with pytest.raises(spm.SpmError) as e:
         spm.spmttkrp_plan_repartition(p0, 70000)
     assert e.value.status == 1
+
+
+def test_plan_autotune_picks_a_candidate_and_keeps_parity():
+    dims = (3000, 800, 150)
+    _, idx, vals = synth.coo_distinct(dims, 200000, (1.2, 1.2, None), seed=31)
+    Y = synth.factors(dims, 32, seed=31)
+    plan, _, dfac = run_all_modes(dims, idx, vals, Y)
+    sms = spm.spm_device_sm_count()
+    chosen, ms = spm.spmttkrp_plan_autotune(plan, dfac, [sms, 2 * sms, 7], reps=2)
+    assert chosen in (sms, 2 * sms, 7) and all(m > 0 for m in ms)
+    check_copies(plan, idx, kappa=chosen)
+    for d in range(3):
+        out = torch.full((dims[d], 32), float("nan"), device="cuda")
+        spm.spmttkrp_run(plan, d, dfac, out)
+        assert rel(out.cpu().numpy(), oracle.mttkrp(dims, idx, vals, Y, d)) < TOL
+    chosen2, ms2 = spm.spmttkrp_plan_autotune(plan, dfac)  # default candidates
+    assert chosen2 in (sms, 2 * sms) and len(ms2) == 2
+    assert spm.spmttkrp_plan_status(plan) == 0
