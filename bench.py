@@ -50,7 +50,7 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="scale",
-                    choices=["scale", "batching", "serving", "precision", "schemes"],
+                    choices=["scale", "batching", "serving", "precision", "five", "schemes"],
                     help="scale (default, the headline line); the others print their "
                          "own JSON line")
     ap.add_argument("--tensors", type=int, default=512, help="batching: tensor count")
@@ -252,7 +252,7 @@ def main():
     if args.workload != "scale":
         if rank == 0:  # the extra workloads run on one GPU
             {"batching": run_batching, "serving": run_serving, "precision": run_precision,
-             "schemes": run_schemes}[args.workload](args, rank, world)
+             "five": run_precision, "schemes": run_schemes}[args.workload](args, rank, world)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
@@ -731,6 +731,8 @@ def run_precision(args, rank, world):
     """Precision workload: 4-mode 20,000 x 20,000 x 5,000 x 24 COO, 100M
     nonzeros (Zipf(1.0) x3 + uniform, lognormal values), R = 64, factors
     stored in FP32 or BF16 with FP32 accumulation; Gram/Cholesky in FP64.
+    With --workload five the same measurement runs on the 5-mode preset
+    (165,400 x 11,400 x 2 x 100 x 89, 26M nonzeros, R = 32).
 
     Reports per arm: spMTTKRP time and algorithmic GB/s per mode (inputs
     resident, larger than L2), the error of sampled output rows against the
@@ -743,7 +745,8 @@ def run_precision(args, rank, world):
     import oracle
     import synth
     import paper_2503_18198_gb300 as spm
-    dims, idx, vals, R, Y = synth.preset_torch("precision", device="cuda")
+    name_w = "five" if args.workload == "five" else "precision"
+    dims, idx, vals, R, Y = synth.preset_torch(name_w, device="cuda")
     N = len(dims)
     nnz = int(vals.numel())
     distinct = distinct_counts(idx)
@@ -831,11 +834,13 @@ def run_precision(args, rank, world):
         del fac, outs
     clk = clocks.stop()
     line = {
-        "workload": "precision", "metric": "spMTTKRP GB/s per mode, FP32 vs BF16 factors",
+        "workload": name_w, "metric": "spMTTKRP GB/s per mode, FP32 vs BF16 factors",
         "unit": "GB/s", "value": arms["bf16"]["mttkrp_GBs_all_modes"], "higher_is_better": True,
         "n_gpus": 1, "data": "synthetic",
         "config": {"dims": list(dims), "nnz": nnz, "rank": R, "sweeps": args.sweeps,
-                   "coords": "Zipf(1.0) x3 + uniform", "values": "lognormal(0,1)",
+                   "coords": "Zipf(1.0) x3 + uniform" if name_w == "precision" else
+                             "Zipf(1.1) x2 + uniform x3",
+                   "values": "lognormal(0,1)" if name_w == "precision" else "U(0,1)",
                    "l2": "inputs larger than L2", "peak": peak, "peak_source": peak_kind,
                    "sampled_rows_per_mode": [int(r.size) for r in rows]},
         "arms": arms, "fit_bf16_minus_fp32": fits["bf16"] - fits["fp32"],

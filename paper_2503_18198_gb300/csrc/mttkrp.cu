@@ -12,8 +12,11 @@ MttkrpKernelFn pick_mttkrp_f32_a(int nin, int R);
 MttkrpKernelFn pick_mttkrp_f32_b(int nin, int R);
 MttkrpKernelFn pick_mttkrp_bf16_a(int nin, int R);
 MttkrpKernelFn pick_mttkrp_bf16_b(int nin, int R);
+MttkrpKernelFn pick_mttkrp_f32_c(int R);
+MttkrpKernelFn pick_mttkrp_bf16_c(int R);
 
 MttkrpKernelFn pick_mttkrp(bool bf16, int nin, int R) {
+  if (nin == 4) return bf16 ? pick_mttkrp_bf16_c(R) : pick_mttkrp_f32_c(R);
   if (bf16) return nin <= 2 ? pick_mttkrp_bf16_a(nin, R) : pick_mttkrp_bf16_b(nin, R);
   return nin <= 2 ? pick_mttkrp_f32_a(nin, R) : pick_mttkrp_f32_b(nin, R);
 }

@@ -1,4 +1,4 @@
-// BF16-factor MTTKRP instantiations, 4 modes and the generic >= 5 modes.
+// BF16-factor MTTKRP instantiations, 4 modes and the generic >= 6 modes.
 #include "mttkrp_inst.cuh"
 
 namespace spm {

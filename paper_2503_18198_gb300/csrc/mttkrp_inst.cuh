@@ -30,7 +30,7 @@ MttkrpKernelFn pick_mttkrp_t(int R) {
   return &mttkrp_kernel<RI, NIN, FT, 1, 32, 8>;
 }
 
-// The generic-N variant (five or more modes) only has the scalar shape.
+// The generic-N variant (six or more modes) only has the scalar shape.
 template <typename FT>
 MttkrpKernelFn pick_mttkrp_generic_t(int) {
   return &mttkrp_kernel<2, 0, FT, 1, 32, 8>;

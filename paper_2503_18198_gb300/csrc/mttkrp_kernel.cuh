@@ -202,7 +202,7 @@ __device__ __forceinline__ void store_vec(float* row_ptr, int R, int r0, const f
   }
 }
 
-// NIN > 0: exactly NIN input modes.  NIN == 0: runtime a.nin (five or more
+// NIN > 0: exactly NIN input modes.  NIN == 0: runtime a.nin (six or more
 // modes); the first two input modes are batched, further ones are fetched
 // when the step is computed.
 //

@@ -19,6 +19,9 @@ available here:
                  uniform, 100M distinct coordinates, values lognormal(0,1),
                  R = 64.
 
+* ``five``       5 modes 165,400 x 11,400 x 2 x 100 x 89 (the shape of the
+                 paper's 5-mode tensor), modes 0-1 Zipf(1.1), the short modes
+                 uniform, 26M distinct coordinates, values U(0,1), R = 32.
 * ``batching``   512 independent 3-mode tensors, each dim log-uniform in
                  [100, 20,000], nnz log-uniform in [1e3, 2e6] (at most half
                  the cells, so that distinct coordinates can be drawn),
@@ -43,6 +46,9 @@ PRESETS = {
     "precision": dict(dims=(20_000, 20_000, 5_000, 24), nnz=100_000_000,
                       alphas=(1.0, 1.0, 1.0, None), values="lognormal",
                       rank=64, seed=3),
+    "five": dict(dims=(165_400, 11_400, 2, 100, 89), nnz=26_000_000,
+                 alphas=(1.1, 1.1, None, None, None), values="uniform", rank=32,
+                 seed=6),
 }
 
 
