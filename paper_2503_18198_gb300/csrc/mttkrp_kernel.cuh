@@ -89,31 +89,16 @@ enum : int {
 #ifndef SPM_MT_REUSE
 #define SPM_MT_REUSE 0  // 1: a slot keeps its first input mode's row and skips a repeated gather
 #endif
-#ifndef SPM_MT_CONTIG
-#define SPM_MT_CONTIG 0  // 1: slots stream contiguous sub-ranges of a unit
-#endif
-
-// Floats of one warp's slot-head buffer: G slots x R ranks, G = 32 / LPN for
-// the lane layout the kernel picks for (R, factor element size).
-inline int mttkrp_head_floats(int R, int fsize) {
-  const int vec = 16 / fsize;
-  if (R % vec == 0) {
-    const int lpn = R / vec;
-    if (lpn <= 32 && (lpn & (lpn - 1)) == 0) return (32 / lpn) * R;
-    if (lpn == 64) return R;
-  }
-  return R;
-}
-
 // Shared memory of one block: per-warp rings of record tiles and their
-// barriers, two boundary partials (+ row ids) per work unit, and with
-// contiguous slots each warp's slot-head partials.
+// barriers, and two boundary partials (+ row ids) per work unit.  A stage
+// tile has the same bytes for either record size; the factor type does not
+// enter.
 inline size_t mttkrp_smem_bytes(int R, int RI, int nu, int fsize) {
-  (void)RI;  // a stage tile has the same bytes for either record size
+  (void)RI;
+  (void)fsize;
   return (size_t)MT_WARPS * MT_STAGES * MT_TILE_RECS * 16 +
          (size_t)MT_WARPS * MT_STAGES * sizeof(uint64_t) + (size_t)2 * nu * R * sizeof(float) +
-         (size_t)2 * nu * sizeof(int) +
-         (SPM_MT_CONTIG ? (size_t)MT_WARPS * mttkrp_head_floats(R, fsize) * sizeof(float) : 0);
+         (size_t)2 * nu * sizeof(int);
 }
 
 // Raw 32-bit words of one lane's slice of a factor row, and their conversion.
@@ -209,8 +194,7 @@ __device__ __forceinline__ void store_vec(float* row_ptr, int R, int r0, const f
 // mttkrp_partition processes partition z of one mode copy with the whole
 // thread block (every thread must call it); it is the body of the
 // single-tensor kernel and of the batched persistent kernel.
-template <int RI, int NIN, typename FT, int VEC, int LPN, int CPL,
-          bool CONTIG = (SPM_MT_CONTIG != 0) && (NIN > 0)>
+template <int RI, int NIN, typename FT, int VEC, int LPN, int CPL>
 __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int z) {
   using S = Slice<FT, VEC>;
   constexpr int RAWN = S::RAWN;
@@ -243,7 +227,6 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
   float* part = reinterpret_cast<float*>(smem + (size_t)MT_WARPS * MT_STAGES * tile_bytes +
                                          (size_t)MT_WARPS * MT_STAGES * sizeof(uint64_t));
   int* prow = reinterpret_cast<int*>(part + (size_t)2 * NU * R);  // [2 * NU]
-  float* hbuf = reinterpret_cast<float*>(prow + 2 * NU) + (size_t)warp * G * R;  // [G][R]
 
   auto row_at = [&](int64_t k) -> int { return __ldg(&a.rec[k * RI].x); };
   auto rank0 = [&](int c) -> int { return (c * LPN + sub) * VEC; };
@@ -283,224 +266,7 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
     const int lenw = (int)(k1 - k0);
     float* pf = part + (size_t)(2 * u) * R;
     float* pl = pf + R;
-    if (CONTIG && lenw > 0) {
-      // ---- contiguous slots: slot s streams copy positions [b_s, b_{s+1})
-      // of the unit, b_s = k0 + floor(s * len / G).  Each slot keeps the
-      // factor rows of its last nonzero and gathers a mode's row only when
-      // that index changes (the copy order makes the first input index
-      // repeat along a fibre).  A finished row is stored by the slot; its
-      // first row (which may have begun in the previous slot) goes to the
-      // warp's head buffer and its open row is kept to the end of the unit.
-      constexpr int CH = TILE / G;  // records per slot per tile
-      constexpr int UB = (NIN * CPL * RAWN <= 8) ? 2 : 1;  // steps per batch
-      auto slot_begin = [&](int s) -> int64_t { return k0 + ((int64_t)lenw * s) / G; };
-      const int64_t sb = slot_begin(slot);
-      const int slen = (int)(slot_begin(slot + 1) - sb);
-      const int maxlen = (lenw + G - 1) / G;
-      const int ntiles = (maxlen + CH - 1) / CH;
-      const int seq0 = seq_issued;
-      auto issue = [&](int t) {  // lane 0 only
-        uint32_t bytes = 0;
-        for (int s = 0; s < G; ++s) {
-          const int64_t from = slot_begin(s) + (int64_t)t * CH;
-          const int64_t cnt = min((int64_t)CH, max((int64_t)0, slot_begin(s + 1) - from));
-          bytes += (uint32_t)(cnt * 16 * RI);
-        }
-        const int q = seq0 + t;
-        uint64_t* bar = &bars[q % MT_STAGES];
-        mbar_arrive_expect_tx(bar, bytes);
-        for (int s = 0; s < G; ++s) {
-          const int64_t from = slot_begin(s) + (int64_t)t * CH;
-          const int64_t cnt = min((int64_t)CH, max((int64_t)0, slot_begin(s + 1) - from));
-          if (cnt > 0)
-            bulk_g2s(stages + (q % MT_STAGES) * tile_bytes + (size_t)s * CH * 16 * RI,
-                     a.rec + from * RI, (uint32_t)(cnt * 16 * RI), bar);
-        }
-      };
-      int issued = ntiles < MT_STAGES ? ntiles : MT_STAGES;
-      if (lane == 0) {
-        fence_proxy_async_smem();  // the previous unit's merge wrote the stages
-        for (int t = 0; t < issued; ++t) issue(t);
-      }
-      int cur = -1;             // this slot's open row
-      int head_row = -1;        // its first row, once finished
-      constexpr int NINC = NIN > 0 ? NIN : 1;  // array extent (NIN == 0 never takes this path)
-      int lastc[NINC];
-      uint32_t ycur[NINC][CPL][RAWN];
-#pragma unroll
-      for (int m = 0; m < NIN; ++m) {
-        lastc[m] = -1;
-#pragma unroll
-        for (int c = 0; c < CPL; ++c)
-#pragma unroll
-          for (int i = 0; i < RAWN; ++i) ycur[m][c][i] = 0u;
-      }
-      float acc[CPL][VEC];
-#pragma unroll
-      for (int c = 0; c < CPL; ++c)
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) acc[c][e] = 0.f;
-      float* hb = hbuf + (size_t)slot * R;
-
-      for (int t = 0; t < ntiles; ++t) {
-        if (t > 0) {
-          __syncwarp();  // every lane is done with tile t-1: refill its stage
-          if (issued < ntiles) {
-            if (lane == 0) {
-              fence_proxy_async_smem();
-              issue(issued);
-            }
-            ++issued;
-          }
-        }
-        {
-          const int q = seq0 + t;
-          const bool ok = mbar_wait_bounded(&bars[q % MT_STAGES], (uint32_t)((q / MT_STAGES) & 1));
-          timeout = __any_sync(SPM_FULL_MASK, !ok);
-        }
-        if (timeout) {
-          for (int q = seq0 + t + 1; q < seq0 + issued; ++q)
-            (void)mbar_wait_bounded(&bars[q % MT_STAGES], (uint32_t)((q / MT_STAGES) & 1), 1u << 20);
-          if (lane == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
-          break;
-        }
-        const int4* recs = reinterpret_cast<const int4*>(
-            stages + ((seq0 + t) % MT_STAGES) * tile_bytes + (size_t)slot * CH * 16 * RI);
-        const int n = min(CH, max(0, slen - t * CH));          // this slot's records
-        const int nmax = min(CH, max(0, maxlen - t * CH));     // the warp's longest
-        for (int j = 0; j < nmax; j += UB) {
-          int w[UB][W];
-          bool valid[UB];
-          bool need[UB][NINC];
-          uint32_t y[UB][NINC][CPL][RAWN];
-#pragma unroll
-          for (int uu = 0; uu < UB; ++uu) {
-            valid[uu] = j + uu < n;
-#pragma unroll
-            for (int qq = 0; qq < W; ++qq) w[uu][qq] = 0;
-            if (valid[uu]) {
-#pragma unroll
-              for (int qq = 0; qq < RI; ++qq) {
-                const int4 v4 = recs[(j + uu) * RI + qq];
-                w[uu][4 * qq] = v4.x; w[uu][4 * qq + 1] = v4.y;
-                w[uu][4 * qq + 2] = v4.z; w[uu][4 * qq + 3] = v4.w;
-              }
-            }
-          }
-#pragma unroll
-          for (int m = 0; m < NIN; ++m) {
-            int prev = lastc[m];
-#pragma unroll
-            for (int uu = 0; uu < UB; ++uu) {
-              const int c = w[uu][1 + m];
-              need[uu][m] = valid[uu] && c != prev;
-              if (valid[uu]) prev = c;
-            }
-            lastc[m] = prev;
-          }
-#pragma unroll
-          for (int uu = 0; uu < UB; ++uu)
-#pragma unroll
-            for (int m = 0; m < NIN; ++m)
-              if (need[uu][m]) {
-#pragma unroll
-                for (int c = 0; c < CPL; ++c) S::load(a.fac[m], w[uu][1 + m], R, rank0(c), y[uu][m][c]);
-              }
-#pragma unroll
-          for (int uu = 0; uu < UB; ++uu) {
-            if (!valid[uu]) break;
-#pragma unroll
-            for (int m = 0; m < NIN; ++m)
-              if (need[uu][m]) {
-#pragma unroll
-                for (int c = 0; c < CPL; ++c)
-#pragma unroll
-                  for (int i = 0; i < RAWN; ++i) ycur[m][c][i] = y[uu][m][c][i];
-              }
-            const int row = w[uu][0];
-            if (row != cur) {  // this slot's row `cur` ended
-              if (cur >= 0) {
-                float* dst = head_row < 0 ? hb : a.out + (int64_t)cur * R;
-                if (head_row < 0) head_row = cur;
-#pragma unroll
-                for (int c = 0; c < CPL; ++c) store_vec<VEC>(dst, R, rank0(c), acc[c]);
-#pragma unroll
-                for (int c = 0; c < CPL; ++c)
-#pragma unroll
-                  for (int e = 0; e < VEC; ++e) acc[c][e] = 0.f;
-              }
-              cur = row;
-            }
-            const float val = __int_as_float(w[uu][NIN + 1]);
-#pragma unroll
-            for (int c = 0; c < CPL; ++c) {
-              float f[VEC], g[VEC];
-              S::cvt(ycur[0][c], f);
-#pragma unroll
-              for (int e = 0; e < VEC; ++e) g[e] = val * f[e];
-#pragma unroll
-              for (int m = 1; m < NIN - 1; ++m) {
-                S::cvt(ycur[m][c], f);
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) g[e] *= f[e];
-              }
-              if (NIN > 1) {
-                S::cvt(ycur[NIN - 1][c], f);
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) acc[c][e] = fmaf(g[e], f[e], acc[c][e]);
-              } else {
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) acc[c][e] += g[e];
-              }
-            }
-          }
-        }
-      }
-      // ---- merge of the slots' head and open-row partials, in copy order
-      __syncwarp();
-      float* tb = reinterpret_cast<float*>(stages);  // all tiles consumed: scratch
-      int* srow = reinterpret_cast<int*>(tb + (size_t)G * R);  // [G][2] head, open row
-      if (slen > 0) {
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) store_vec<VEC>(tb + (size_t)slot * R, R, rank0(c), acc[c]);
-      }
-      if (sub == 0) {
-        srow[2 * slot] = head_row;
-        srow[2 * slot + 1] = slen > 0 ? cur : -1;
-      }
-      __syncwarp();
-      const int first_row = row_at(k0);
-      for (int r = lane; r < R; r += 32) {
-        float cval = 0.f;
-        int crow = -1;
-        for (int e = 0; e < 2 * G; ++e) {
-          const int row = srow[e];
-          if (row < 0) continue;
-          const float v = (e & 1) ? tb[(size_t)(e >> 1) * R + r] : hbuf[(size_t)(e >> 1) * R + r];
-          if (row == crow) {
-            cval += v;
-          } else {
-            if (crow >= 0) (crow == first_row ? pf : a.out + (int64_t)crow * R)[r] = cval;
-            crow = row;
-            cval = v;
-          }
-        }
-        if (crow == first_row) {
-          pf[r] = cval;
-          pl[r] = 0.f;
-        } else {
-          pl[r] = cval;
-        }
-      }
-      if (lane == 0) {
-        int last = -1;
-        for (int e = 2 * G - 1; e >= 0 && last < 0; --e) last = srow[e];
-        prow[2 * u] = first_row;
-        prow[2 * u + 1] = last != first_row ? last : -1;
-      }
-      __syncwarp();  // srow / tb read before the next unit's copies land
-      seq_issued = seq0 + ntiles;
-    } else if (lenw > 0) {
+    if (lenw > 0) {
       const int ntiles = (lenw + TILE - 1) / TILE;
       const int seq0 = seq_issued;  // ring sequence number of this unit's tile 0
       auto issue = [&](int t) {     // lane 0 only
