@@ -412,6 +412,19 @@ spm_status spm_server_usage(spm_server_t server, size_t *used, size_t *budget);
 
 void spm_server_destroy(spm_server_t server);
 
+/* ---- failure-detection hooks (tests) ----------------------------------------- */
+
+/* Launch a kernel whose bounded wait on an mbarrier that nothing completes
+ * gives up after `limit` polls (the same wait the MTTKRP kernel uses for its
+ * record copies); returns SPM_ERR_TIMEOUT when the timeout was recorded, as
+ * expected, with the CUDA context still usable.  Synchronises `stream`. */
+spm_status spm_selftest_wait_timeout(uint32_t limit, void *stream);
+
+/* Fault injection on the host: the k-th device allocation made for a plan
+ * from now on (k = 0: the next one) fails as if cudaMalloc had run out of
+ * memory; k < 0 disables.  One-shot.  For tests of the error paths. */
+void spm_inject_alloc_failure(int k);
+
 /* Synchronise `stream` and return the plan's sticky device-side error
  * (SPM_OK, SPM_ERR_NUMERIC or SPM_ERR_TIMEOUT), then clear it. */
 spm_status spmttkrp_plan_status(spmttkrp_plan_t plan, void *stream);

@@ -63,7 +63,7 @@ SYMBOLS = ("spmttkrp_plan", "spmttkrp_plan_bytes", "spmttkrp_plan_permutation",
            "spm_batch_status", "spm_batch_destroy", "spm_batch_autotune",
            "spmttkrp_plan_bytes_estimate", "spm_server_create", "spm_server_submit",
            "spm_server_step", "spm_server_job", "spm_server_result", "spm_server_usage",
-           "spm_server_destroy")
+           "spm_server_destroy", "spm_selftest_wait_timeout", "spm_inject_alloc_failure")
 
 
 def library_path() -> str:
@@ -137,6 +137,10 @@ def load(build_if_missing: bool = False):
     lib.spm_server_usage.restype = i32
     lib.spm_server_destroy.argtypes = [P]
     lib.spm_server_destroy.restype = None
+    lib.spm_selftest_wait_timeout.argtypes = [u32, P]
+    lib.spm_selftest_wait_timeout.restype = i32
+    lib.spm_inject_alloc_failure.argtypes = [i32]
+    lib.spm_inject_alloc_failure.restype = None
     lib.spm_batch_destroy.argtypes = [P]
     lib.spm_batch_destroy.restype = None
     lib.spm_device_sm_count.argtypes = []
@@ -519,3 +523,13 @@ class Server:
             self.destroy()
         except Exception:
             pass
+
+
+def spm_selftest_wait_timeout(limit: int = 4096, stream=None) -> int:
+    """Status of the bounded-wait self-test (SPM_ERR_TIMEOUT expected)."""
+    return int(load().spm_selftest_wait_timeout(int(limit), _stream(stream)))
+
+
+def spm_inject_alloc_failure(k: int):
+    """Make the k-th plan allocation from now fail with SPM_ERR_OOM (k < 0: off)."""
+    load().spm_inject_alloc_failure(int(k))

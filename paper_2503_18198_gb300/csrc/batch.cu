@@ -412,6 +412,7 @@ spm_status spm_batch_create(spm_batch_t* out, int ntensors, const spmttkrp_plan_
 }
 
 spm_status spm_batch_sweep(spm_batch_t B, void* stream) {
+  NvtxScope nv("spm_batch_sweep");
   if (!B) return SPM_ERR_INVALID_ARG;
   return batch_sweep(B, static_cast<cudaStream_t>(stream));
 }

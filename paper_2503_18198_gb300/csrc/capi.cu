@@ -11,6 +11,7 @@ namespace spm {
 spm_status plan_alloc(spmttkrp_plan_s* p, void** ptr, size_t bytes) {
   *ptr = nullptr;
   if (p->nallocs >= (int)(sizeof(p->allocs) / sizeof(p->allocs[0]))) return SPM_ERR_OOM;
+  if (alloc_fault_due()) return SPM_ERR_OOM;  // injected by spm_inject_alloc_failure
   if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMalloc(ptr, bytes);
   if (e != cudaSuccess) {
@@ -103,6 +104,7 @@ int spm_device_sm_count(void) { return sm_count(); }
 spm_status spmttkrp_plan(spmttkrp_plan_t* out, int nmodes, const int64_t* dims, int64_t nnz,
                          const int32_t* const* idx, const float* vals, int rank,
                          uint32_t flags, void* stream) {
+  NvtxScope nv("spmttkrp_plan");
   if (!out) return SPM_ERR_INVALID_ARG;
   *out = nullptr;
   if (nmodes < 2 || nmodes > SPM_MAX_MODES || !dims || nnz < 0 ||
@@ -281,12 +283,14 @@ void spmttkrp_plan_destroy(spmttkrp_plan_t plan) {
 
 spm_status spmttkrp_run(spmttkrp_plan_t plan, int mode, const void* const* factors, float* out,
                         void* stream) {
+  NvtxScope nv("spmttkrp_run");
   if (!plan) return SPM_ERR_INVALID_ARG;
   return run_mttkrp(plan, mode, factors, out, static_cast<cudaStream_t>(stream));
 }
 
 spm_status cpd_als_step(spmttkrp_plan_t plan, void* const* factors, double* lambda, double* fit,
                         void* stream) {
+  NvtxScope nv("cpd_als_step");
   if (!plan || !factors || !lambda) return SPM_ERR_INVALID_ARG;
   return als_sweep(plan, factors, lambda, fit, static_cast<cudaStream_t>(stream));
 }

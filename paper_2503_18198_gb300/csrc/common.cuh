@@ -26,6 +26,8 @@
     if (spm_s_ != SPM_OK) return spm_s_; \
   } while (0)
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace spm {
 
 // Words per nonzero record of a mode copy: c_d, the N-1 input-mode indices in
@@ -217,6 +219,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
+
+// NVTX range for the duration of a host scope (shown by profilers that
+// record NVTX; free otherwise).
+struct NvtxScope {
+  explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+  NvtxScope(const NvtxScope&) = delete;
+  NvtxScope& operator=(const NvtxScope&) = delete;
+};
 
 template <typename T>
 __host__ __device__ inline T ceil_div(T a, T b) {

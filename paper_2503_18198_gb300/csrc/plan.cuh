@@ -95,6 +95,10 @@ spm_status ensure_als_state(spmttkrp_plan_s* p);
 
 int sm_count();
 
+// True when an allocation failure injected by spm_inject_alloc_failure is
+// due now (diag.cu).
+bool alloc_fault_due();
+
 // Partition count of a plan made with SPM_KAPPA(0): SPM_PARTITIONS_PER_SM
 // per SM (-1 when the device cannot be queried).
 int default_kappa();

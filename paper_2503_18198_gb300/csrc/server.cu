@@ -232,6 +232,7 @@ spm_status spm_server_submit(spm_server_t S, const spm_job_desc* d, int64_t* job
 }
 
 spm_status spm_server_step(spm_server_t S, int* running, int* queued) {
+  NvtxScope nv("spm_server_step");
   if (!S) return SPM_ERR_INVALID_ARG;
   spm_batch_s* B = S->B;
   // 1. one sweep of every running job (asynchronous)
