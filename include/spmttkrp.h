@@ -244,12 +244,21 @@ spm_status spmttkrp_run_noalloc(int nmodes, const int64_t *dims, int64_t nnz,
  *
  * The Gram of each factor is cached in the plan and refreshed after its
  * update; the cache is (re)built from `factors` on the first call and
- * whenever the factor pointers change.  If V is not numerically positive
- * definite the sweep stops at that mode, later calls return
- * SPM_ERR_NUMERIC, and spmttkrp_plan_status reports it (the check is
- * device-side, so it is seen at the next synchronising call). */
+ * whenever the factor pointers change.  A caller that writes the factors
+ * itself between calls (a restart, a checkpoint restored into the same
+ * buffers) calls cpd_als_reset first.  If V is not numerically positive
+ * definite (or not finite) the sweep stops at that mode, the device-side
+ * error flag makes the plan's later sweeps skip their work, and
+ * spmttkrp_plan_status reports SPM_ERR_NUMERIC and clears the flag (the
+ * check is device-side, so it is seen at the next synchronising call).
+ * The CP-ALS state is the factors and lambda, both the caller's: a run
+ * resumed from copies of them continues bitwise as the uninterrupted one. */
 spm_status cpd_als_step(spmttkrp_plan_t plan, void *const *factors,
                         double *lambda, double *fit, void *stream);
+
+/* Forget the cached Grams: the next cpd_als_step rebuilds them from its
+ * factors.  Host only. */
+spm_status cpd_als_reset(spmttkrp_plan_t plan);
 
 /* Device bytes a plan of this shape holds once cpd_als_step has run on it
  * (*resident: mode copies, partitions, MTTKRP and CP-ALS workspace; equals
@@ -400,6 +409,20 @@ spm_status spm_server_submit(spm_server_t server, const spm_job_desc *desc, int6
 spm_status spm_server_step(spm_server_t server, int *running, int *queued);
 
 spm_status spm_server_job(spm_server_t server, int64_t job, spm_job_info *info);
+
+/* Checkpoint of a running job between steps: its factors (stored type,
+ * device, NULL entries skipped), weights (device double[R], may be NULL),
+ * sweeps done and the fit of its last sweep (host).  Synchronises `stream`. */
+spm_status spm_server_snapshot(spm_server_t server, int64_t job, void *const *factors,
+                               double *lambda, int *sweeps, double *prev_fit, void *stream);
+
+/* Queue a job resumed from a snapshot: desc->init holds the snapshot's
+ * factors as FP32 (exact for BF16 ones), `sweeps_done` and `prev_fit` the
+ * snapshot's counters (0 <= sweeps_done < desc->max_sweeps).  On a server
+ * with the same flags and nnz_per_partition the job then finishes bitwise as
+ * it would have without the interruption. */
+spm_status spm_server_resume(spm_server_t server, const spm_job_desc *desc, int sweeps_done,
+                             double prev_fit, int64_t *job);
 
 /* Copy a finished job's factors (stored type, device, NULL entries skipped)
  * and weights (device double[R], may be NULL) out on `stream`, synchronise,

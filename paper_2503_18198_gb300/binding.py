@@ -63,7 +63,8 @@ SYMBOLS = ("spmttkrp_plan", "spmttkrp_plan_bytes", "spmttkrp_plan_permutation",
            "spm_batch_status", "spm_batch_destroy", "spm_batch_autotune",
            "spmttkrp_plan_bytes_estimate", "spm_server_create", "spm_server_submit",
            "spm_server_step", "spm_server_job", "spm_server_result", "spm_server_usage",
-           "spm_server_destroy", "spm_selftest_wait_timeout", "spm_inject_alloc_failure")
+           "spm_server_destroy", "spm_selftest_wait_timeout", "spm_inject_alloc_failure",
+           "cpd_als_reset", "spm_server_snapshot", "spm_server_resume")
 
 
 def library_path() -> str:
@@ -141,6 +142,12 @@ def load(build_if_missing: bool = False):
     lib.spm_selftest_wait_timeout.restype = i32
     lib.spm_inject_alloc_failure.argtypes = [i32]
     lib.spm_inject_alloc_failure.restype = None
+    lib.cpd_als_reset.argtypes = [P]
+    lib.cpd_als_reset.restype = i32
+    lib.spm_server_snapshot.argtypes = [P, i64, P, P, P, P, P]
+    lib.spm_server_snapshot.restype = i32
+    lib.spm_server_resume.argtypes = [P, P, i32, ctypes.c_double, P]
+    lib.spm_server_resume.restype = i32
     lib.spm_batch_destroy.argtypes = [P]
     lib.spm_batch_destroy.restype = None
     lib.spm_device_sm_count.argtypes = []
@@ -298,6 +305,11 @@ def cpd_als_step(plan: Plan, factors, lam, fit=None, stream=None):
                                ctypes.c_void_p(fit.data_ptr() if fit is not None else 0),
                                _stream(stream)),
            "cpd_als_step")
+
+
+def cpd_als_reset(plan: Plan):
+    """Forget the plan's cached Grams (after writing the factors oneself)."""
+    _check(load().cpd_als_reset(plan.handle), "cpd_als_reset")
 
 
 def spmttkrp_plan_status(plan: Plan, stream=None) -> int:
@@ -459,9 +471,11 @@ class Server:
         self.shapes = {}
 
     def submit(self, dims, idx, vals, rank: int, init, tol: float = 1e-4,
-               max_sweeps: int = 50) -> int:
+               max_sweeps: int = 50, resume=None) -> int:
         """idx: N int32 CUDA tensors, vals float32 CUDA, init: N float32 CUDA
-        [I_w, R].  The producing stream must be synchronised first."""
+        [I_w, R].  The producing stream must be synchronised first.
+        resume = (sweeps_done, prev_fit) from a snapshot continues that job
+        (init then holds the snapshot's factors as FP32)."""
         N = len(dims)
         dims_a = (ctypes.c_int64 * N)(*[int(d) for d in dims])
         idx_a = (ctypes.c_void_p * N)(*[c.data_ptr() for c in idx])
@@ -472,8 +486,13 @@ class Server:
                     vals.data_ptr() if nnz else None, int(rank),
                     ctypes.cast(init_a, ctypes.c_void_p).value, float(tol), int(max_sweeps))
         job = ctypes.c_int64()
-        _check(load().spm_server_submit(self.handle, ctypes.byref(d), ctypes.byref(job)),
-               "spm_server_submit")
+        if resume is None:
+            _check(load().spm_server_submit(self.handle, ctypes.byref(d), ctypes.byref(job)),
+                   "spm_server_submit")
+        else:
+            _check(load().spm_server_resume(self.handle, ctypes.byref(d), int(resume[0]),
+                                            float(resume[1]), ctypes.byref(job)),
+                   "spm_server_resume")
         j = int(job.value)
         self._inputs[j] = (idx, vals, init)
         self.ranks[j] = int(rank)
@@ -506,6 +525,20 @@ class Server:
                                         ctypes.c_void_p(lam.data_ptr()), _stream(stream)),
                "spm_server_result")
         return fac, lam
+
+    def snapshot(self, job: int, stream=None):
+        """(factors, lambda, sweeps_done, prev_fit) of a running job, between steps."""
+        import torch
+        dt = torch.bfloat16 if self.flags & SPM_FACTOR_BF16 else torch.float32
+        R = self.ranks[job]
+        fac = [torch.empty(n, R, dtype=dt, device="cuda") for n in self.shapes[job]]
+        lam = torch.empty(R, dtype=torch.float64, device="cuda")
+        sw, pf = ctypes.c_int(), ctypes.c_double()
+        _check(load().spm_server_snapshot(self.handle, int(job), _ptrs(fac),
+                                          ctypes.c_void_p(lam.data_ptr()), ctypes.byref(sw),
+                                          ctypes.byref(pf), _stream(stream)),
+               "spm_server_snapshot")
+        return fac, lam, int(sw.value), float(pf.value)
 
     def usage(self):
         u, b = ctypes.c_size_t(), ctypes.c_size_t()

@@ -143,8 +143,10 @@ spm_status grow(T** buf, size_t* cap, size_t need) {
 }  // namespace
 
 spm_status batch_add(spm_batch_s* B, spmttkrp_plan_s* p, void* const* factors, double* lambda,
-                     double* fit, double tol, int max_sweeps, cudaStream_t s) {
-  if (!p || !factors || !lambda || !fit || max_sweeps < 1 || !(tol >= 0.0))
+                     double* fit, double tol, int max_sweeps, cudaStream_t s, int start_sweeps,
+                     double prev_fit) {
+  if (!p || !factors || !lambda || !fit || max_sweeps < 1 || !(tol >= 0.0) || start_sweeps < 0 ||
+      start_sweeps >= max_sweeps)
     return SPM_ERR_INVALID_ARG;
   const int kc = batch_kclass(p->N, p->R);
   if (kc == KC_NONE || (B->bf16 >= 0 && B->bf16 != (int)p->bf16)) return SPM_ERR_UNSUPPORTED;
@@ -178,10 +180,10 @@ spm_status batch_add(spm_batch_s* B, spmttkrp_plan_s* p, void* const* factors, d
   b.lambda_out = lambda;
   b.fit_out = fit;
   b.active = 1;
-  b.sweeps = 0;
+  b.sweeps = start_sweeps;
   b.max_sweeps = max_sweeps;
   b.tol = tol;
-  b.prev_fit = -1.0e300;
+  b.prev_fit = prev_fit;
   for (int w = 0; w < p->N; ++w) b.fac[w] = factors[w];
   for (int d = 0; d < p->N; ++d) {
     const int64_t I = p->dims[d];

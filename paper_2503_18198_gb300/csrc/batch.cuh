@@ -43,8 +43,11 @@ namespace spm {
 // Computes the Grams of its factors on `s` (after pulling the members' state
 // if the device copy is current); the device tables are rebuilt by the next
 // batch_commit.  Factors must stay allocated while it is a member.
+// A resumed tensor starts with `start_sweeps` sweeps done and `prev_fit` as
+// the fit of its last sweep.
 spm_status batch_add(spm_batch_s* B, spmttkrp_plan_s* p, void* const* factors, double* lambda,
-                     double* fit, double tol, int max_sweeps, cudaStream_t s);
+                     double* fit, double tol, int max_sweeps, cudaStream_t s,
+                     int start_sweeps = 0, double prev_fit = -1.0e300);
 
 // Drop member t from the host list (call batch_pull first so that the
 // convergence state of the others is current).

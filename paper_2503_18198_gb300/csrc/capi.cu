@@ -295,6 +295,12 @@ spm_status cpd_als_step(spmttkrp_plan_t plan, void* const* factors, double* lamb
   return als_sweep(plan, factors, lambda, fit, static_cast<cudaStream_t>(stream));
 }
 
+spm_status cpd_als_reset(spmttkrp_plan_t plan) {
+  if (!plan) return SPM_ERR_INVALID_ARG;
+  plan->als.ready = false;
+  return SPM_OK;
+}
+
 spm_status spmttkrp_plan_status(spmttkrp_plan_t plan, void* stream) {
   if (!plan) return SPM_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

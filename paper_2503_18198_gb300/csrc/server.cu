@@ -60,6 +60,8 @@ struct Job {
   double* lamfit = nullptr;  // [R] weights, then the fit
   int sweeps = 0;
   double fit = 0.0;
+  int start_sweeps = 0;          // > 0 for a job resumed from a snapshot
+  double start_prev_fit = -1.0e300;
   double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
 };
 
@@ -289,7 +291,7 @@ spm_status spm_server_step(spm_server_t S, int* running, int* queued) {
   // 4. admitted jobs join the batch
   for (Job* j : admitted) {
     const spm_status st = batch_add(B, j->plan, j->fac, j->lamfit, j->lamfit + j->R, j->tol,
-                                    j->max_sweeps, S->s_sweep);
+                                    j->max_sweeps, S->s_sweep, j->start_sweeps, j->start_prev_fit);
     if (st != SPM_OK) {
       fail(S, j, st);
       continue;
@@ -299,6 +301,43 @@ spm_status spm_server_step(spm_server_t S, int* running, int* queued) {
   }
   if (running) *running = (int)S->running.size();
   if (queued) *queued = (int)S->queue.size();
+  return SPM_OK;
+}
+
+spm_status spm_server_resume(spm_server_t S, const spm_job_desc* d, int sweeps_done,
+                             double prev_fit, int64_t* job) {
+  if (!S || !d || sweeps_done < 0 || sweeps_done >= d->max_sweeps) return SPM_ERR_INVALID_ARG;
+  SPM_TRY(spm_server_submit(S, d, job));
+  Job* j = S->jobs[*job];
+  j->start_sweeps = sweeps_done;
+  j->start_prev_fit = prev_fit;
+  return SPM_OK;
+}
+
+spm_status spm_server_snapshot(spm_server_t S, int64_t job, void* const* factors, double* lambda,
+                               int* sweeps, double* prev_fit, void* stream) {
+  if (!S || !sweeps || !prev_fit) return SPM_ERR_INVALID_ARG;
+  auto it = S->jobs.find(job);
+  if (it == S->jobs.end() || it->second->state != SPM_JOB_RUNNING) return SPM_ERR_INVALID_ARG;
+  Job* j = it->second;
+  int t = 0;
+  while (t < (int)S->running.size() && S->running[t] != j) ++t;
+  if (t == (int)S->running.size()) return SPM_ERR_INVALID_ARG;
+  // the host descriptors are current between steps (pulled after each sweep)
+  const BatchTensor& b = S->B->host[t];
+  *sweeps = b.sweeps;
+  *prev_fit = b.prev_fit;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t sf = (S->flags & SPM_FACTOR_MASK) == SPM_FACTOR_BF16 ? 2 : 4;
+  if (factors)
+    for (int w = 0; w < j->N; ++w)
+      if (factors[w])
+        SPM_CUDA_TRY(cudaMemcpyAsync(factors[w], j->fac[w], sf * (size_t)j->dims[w] * j->R,
+                                     cudaMemcpyDeviceToDevice, s));
+  if (lambda)
+    SPM_CUDA_TRY(cudaMemcpyAsync(lambda, j->lamfit, sizeof(double) * j->R,
+                                 cudaMemcpyDeviceToDevice, s));
+  SPM_CUDA_TRY(cudaStreamSynchronize(s));
   return SPM_OK;
 }
 
