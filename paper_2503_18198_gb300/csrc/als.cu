@@ -87,7 +87,7 @@ spm_status launch_gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, 
     case 4: gram_partial_kernel<FT, 4><<<nb, ALS_THREADS, 0, s>>>(y, I, R, rpb, A.gram_part); break;
     default: return SPM_ERR_UNSUPPORTED;
   }
-  gram_reduce_kernel<<<std::max(1, std::min(64, R * R / 256 + 1)), 256, 0, s>>>(
+  gram_reduce_kernel<<<std::max(1, std::min(1024, R * R / 8)), 256, 0, s>>>(
       A.gram_part, nb, R, G, p->dev_err);
   SPM_CUDA_TRY(cudaGetLastError());
   return SPM_OK;

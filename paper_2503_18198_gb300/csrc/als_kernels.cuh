@@ -45,6 +45,32 @@ __device__ __forceinline__ void df_add_prod2(df& acc, float a, float bh, float b
 }
 __device__ __forceinline__ double df_value(const df& a) { return (double)a.hi + (double)a.lo; }
 
+// Sum of x[0], x[stride], ..., x[(n-1) stride] by one warp in a fixed order:
+// lane l adds elements l, l + 32, ... in turn, then a fixed butterfly over the
+// lanes; lane 0's total is returned to every lane.  The bits do not depend on
+// which warp or launch does the sum.
+__device__ __forceinline__ double warp_sum_strided(const double* __restrict__ x, int n,
+                                                   int64_t stride, int lane) {
+  double s = 0.0;
+  for (int b = lane; b < n; b += 32) s += x[(int64_t)b * stride];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(SPM_FULL_MASK, s, o);
+  return __shfl_sync(SPM_FULL_MASK, s, 0);
+}
+
+// Partial counts up to this are summed by one thread per entry (reads
+// coalesced across entries); more by one warp per entry.  The choice depends
+// on the count only, so a tensor's sums are the same in every launch shape.
+constexpr int ALS_SERIAL_PARTIALS = 64;
+
+// The plan's sticky error flag as seen by lane 0, for every lane of the warp
+// (so that the warp takes one branch around its shuffles).
+__device__ __forceinline__ int warp_err(const int* __restrict__ err) {
+  int e = 0;
+  if ((threadIdx.x & 31) == 0) e = *reinterpret_cast<const volatile int*>(err);
+  return __shfl_sync(SPM_FULL_MASK, e, 0);
+}
+
 template <typename FT>
 __device__ __forceinline__ float load_f(const FT* p, int64_t i);
 template <>
@@ -63,61 +89,75 @@ __device__ __forceinline__ __nv_bfloat16 store_cvt<__nv_bfloat16>(float x) {
 }
 
 // ---------------------------------------------------------------------------
-// Gram partials: block b sums rows [i0, i1) of Y; thread (tr, ts) of a 16x16
-// grid owns entries (tr + 16 a, ts + 16 b).  Requires R <= 16 * GT.
+// Gram partials: block b sums rows [i0, i1) of Y.  Only the lower triangle
+// r >= s is accumulated (G is symmetric): thread t owns entries
+// e = t, t + 256, ... of the R(R+1)/2 triangle entries in row-major order,
+// and mirrors them when it stores.  Requires R <= 16 * GT.
 // ---------------------------------------------------------------------------
 template <typename FT, int GT>
 __device__ __forceinline__ void gram_partial_body(const FT* __restrict__ Y, int64_t I, int R,
                                                   int64_t rows_per_block, double* __restrict__ part,
                                                   int vb) {
-  __shared__ float tile[GRAM_TILE_ROWS][16 * GT + 1];
-  const int tr = threadIdx.x / 16, ts = threadIdx.x % 16;
+  constexpr int RMAX = 16 * GT;
+  constexpr int EPT = (RMAX * (RMAX + 1) / 2 + ALS_THREADS - 1) / ALS_THREADS;  // entries per thread
+  __shared__ float tile[GRAM_TILE_ROWS][RMAX + 1];
   const int64_t i0 = (int64_t)vb * rows_per_block;
   const int64_t i1 = std::min<int64_t>(I, i0 + rows_per_block);
-  df acc[GT][GT];
+  const int T = R * (R + 1) / 2;
+  int er[EPT], es[EPT];
+  df acc[EPT];
 #pragma unroll
-  for (int a = 0; a < GT; ++a)
-#pragma unroll
-    for (int b = 0; b < GT; ++b) acc[a][b] = {0.f, 0.f};
+  for (int k = 0; k < EPT; ++k) {
+    const int e = threadIdx.x + k * ALS_THREADS;
+    int r = 0;
+    while ((r + 1) * (r + 2) / 2 <= e) ++r;  // e = r (r + 1) / 2 + s, s <= r
+    er[k] = e < T ? r : 0;
+    es[k] = e < T ? e - r * (r + 1) / 2 : 0;
+    acc[k] = {0.f, 0.f};
+  }
   for (int64_t t0 = i0; t0 < i1; t0 += GRAM_TILE_ROWS) {
     const int nrow = (int)std::min<int64_t>(GRAM_TILE_ROWS, i1 - t0);
     __syncthreads();
-    for (int e = threadIdx.x; e < GRAM_TILE_ROWS * 16 * GT; e += ALS_THREADS) {
-      const int rr = e / (16 * GT), cc = e % (16 * GT);
+    for (int e = threadIdx.x; e < GRAM_TILE_ROWS * RMAX; e += ALS_THREADS) {
+      const int rr = e / RMAX, cc = e % RMAX;
       tile[rr][cc] = (rr < nrow && cc < R) ? load_f<FT>(Y, (t0 + rr) * R + cc) : 0.f;
     }
     __syncthreads();
     for (int rr = 0; rr < nrow; ++rr) {
-      float ya[GT], yb[GT];
 #pragma unroll
-      for (int a = 0; a < GT; ++a) ya[a] = tile[rr][tr + 16 * a];
-#pragma unroll
-      for (int b = 0; b < GT; ++b) yb[b] = tile[rr][ts + 16 * b];
-#pragma unroll
-      for (int a = 0; a < GT; ++a)
-#pragma unroll
-        for (int b = 0; b < GT; ++b) df_add_prod(acc[a][b], ya[a], yb[b]);
+      for (int k = 0; k < EPT; ++k) df_add_prod(acc[k], tile[rr][er[k]], tile[rr][es[k]]);
     }
   }
   double* out = part + (int64_t)vb * R * R;
 #pragma unroll
-  for (int a = 0; a < GT; ++a)
-#pragma unroll
-    for (int b = 0; b < GT; ++b) {
-      const int r = tr + 16 * a, s = ts + 16 * b;
-      if (r < R && s < R) out[r * R + s] = df_value(acc[a][b]);
+  for (int k = 0; k < EPT; ++k) {
+    const int e = threadIdx.x + k * ALS_THREADS;
+    if (e < T) {
+      const double v = df_value(acc[k]);
+      out[er[k] * R + es[k]] = v;
+      out[es[k] * R + er[k]] = v;
     }
+  }
 }
 
-// G = sum over blocks of the partials (fixed order, FP64).
+// G = sum over blocks of the partials (FP64, fixed order): one warp per
+// entry; virtual block vb of nvb takes every (nvb * warps)-th entry.
 __device__ __forceinline__ void gram_reduce_body(const double* __restrict__ part, int nblocks,
                                                  int R, double* __restrict__ G,
                                                  const int* __restrict__ err, int vb, int nvb) {
-  if (*err) return;
-  for (int e = vb * blockDim.x + threadIdx.x; e < R * R; e += nvb * blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * R * R + e];
-    G[e] = s;
+  if (warp_err(err)) return;
+  if (nblocks <= ALS_SERIAL_PARTIALS) {
+    for (int e = vb * blockDim.x + threadIdx.x; e < R * R; e += nvb * blockDim.x) {
+      double v = 0.0;
+      for (int b = 0; b < nblocks; ++b) v += part[(int64_t)b * R * R + e];
+      G[e] = v;
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = vb * nw + warp; e < R * R; e += nvb * nw) {
+    const double v = warp_sum_strided(part + e, nblocks, (int64_t)R * R, lane);
+    if (lane == 0) G[e] = v;
   }
 }
 
@@ -128,6 +168,10 @@ __device__ __forceinline__ void gram_reduce_body(const double* __restrict__ part
 __device__ __forceinline__ void system_body(const double* __restrict__ grams, int N, int d, int R,
                                             double* __restrict__ V, float* __restrict__ winv,
                                             int* __restrict__ err) {
+  // The R x R working matrix lives in shared memory (R <= 64); `V` is not
+  // used (kept for the callers' argument lists).
+  (void)V;
+  __shared__ double S[64 * 64];
   __shared__ int bad;
   if (threadIdx.x == 0) bad = *err ? 1 : 0;
   __syncthreads();
@@ -137,25 +181,25 @@ __device__ __forceinline__ void system_body(const double* __restrict__ grams, in
     double v = 1.0;
     for (int w = 0; w < N; ++w)
       if (w != d) v *= grams[(int64_t)w * RR + e];
-    V[e] = v;
+    S[e] = v;
   }
   __syncthreads();
-  // right-looking Cholesky, lower triangle of V becomes L
+  // right-looking Cholesky, lower triangle of S becomes L
   for (int j = 0; j < R; ++j) {
     if (threadIdx.x == 0) {
-      const double piv = V[j * R + j];
+      const double piv = S[j * R + j];
       if (!(piv > 0.0) || !isfinite(piv)) bad = 1;
-      else V[j * R + j] = sqrt(piv);
+      else S[j * R + j] = sqrt(piv);
     }
     __syncthreads();
     if (bad) break;
-    const double ljj = V[j * R + j];
-    for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) V[i * R + j] /= ljj;
+    const double ljj = S[j * R + j];
+    for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) S[i * R + j] /= ljj;
     __syncthreads();
     const int m = R - j - 1;  // trailing (m x m) lower triangle update
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
       const int i = j + 1 + e / m, k = j + 1 + e % m;
-      if (k <= i) V[i * R + k] -= V[i * R + j] * V[k * R + j];
+      if (k <= i) S[i * R + k] -= S[i * R + j] * S[k * R + j];
     }
     __syncthreads();
   }
@@ -163,33 +207,29 @@ __device__ __forceinline__ void system_body(const double* __restrict__ grams, in
     if (threadIdx.x == 0) atomicOr(err, DEV_ERR_NUMERIC);
     return;
   }
-  // X = L^{-1} column by column (thread c owns column c), stored in the upper
-  // triangle positions transposed: Xt[c][i] = X[i][c] at V[c*R + i] for i > c
-  // would clash with L, so X goes to winv's scratch as doubles is avoided:
-  // each thread keeps its column in the (unused) strictly upper part of V
-  // reversed: X[i][c] for i >= c is written to V[c * R + i] only for i > c,
-  // and the diagonal 1/L[c][c] is recomputed when needed.
+  // X = L^{-1}, column c by thread c (forward substitution L x = e_c, x_i = 0
+  // for i < c), stored transposed in the strictly upper triangle of S:
+  // X[i][c] at S[c * R + i] for i > c; X[c][c] = 1 / L[c][c] is recomputed.
   for (int c = threadIdx.x; c < R; c += blockDim.x) {
-    // forward substitution L x = e_c, x_i = 0 for i < c
     for (int i = c; i < R; ++i) {
       double s = (i == c) ? 1.0 : 0.0;
       for (int k = c; k < i; ++k) {
-        const double xk = (k == c) ? 1.0 / V[c * R + c] : V[c * R + k];
-        s -= V[i * R + k] * xk;
+        const double xk = (k == c) ? 1.0 / S[c * R + c] : S[c * R + k];
+        s -= S[i * R + k] * xk;
       }
-      const double xi = s / V[i * R + i];
-      if (i > c) V[c * R + i] = xi;
+      const double xi = s / S[i * R + i];
+      if (i > c) S[c * R + i] = xi;
     }
   }
   __syncthreads();
   // W = X^T X:  W[r][s] = sum_{k >= max(r,s)} X[k][r] X[k][s]
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-    const int r = e / R, s = e % R;
-    const int k0 = r > s ? r : s;
+    const int r = e / R, c = e % R;
+    const int k0 = r > c ? r : c;
     double acc = 0.0;
     for (int k = k0; k < R; ++k) {
-      const double xr = (k == r) ? 1.0 / V[r * R + r] : V[r * R + k];
-      const double xs = (k == s) ? 1.0 / V[s * R + s] : V[s * R + k];
+      const double xr = (k == r) ? 1.0 / S[r * R + r] : S[r * R + k];
+      const double xs = (k == c) ? 1.0 / S[c * R + c] : S[c * R + k];
       acc += xr * xs;
     }
     const float hi = (float)acc;
@@ -281,11 +321,19 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ M,
 __device__ __forceinline__ void lambda_body(const double* __restrict__ colsq_part, int nblocks,
                                             int R, double* __restrict__ lambda,
                                             const int* __restrict__ err) {
-  if (*err) return;
-  for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += colsq_part[(int64_t)b * R + r];
-    lambda[r] = sqrt(s);
+  if (warp_err(err)) return;
+  if (nblocks <= ALS_SERIAL_PARTIALS) {
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+      double v = 0.0;
+      for (int b = 0; b < nblocks; ++b) v += colsq_part[(int64_t)b * R + r];
+      lambda[r] = sqrt(v);
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < R; r += nw) {
+    const double v = warp_sum_strided(colsq_part + r, nblocks, R, lane);
+    if (lane == 0) lambda[r] = sqrt(v);
   }
 }
 
@@ -338,17 +386,29 @@ __device__ __forceinline__ void fit_body(const double* __restrict__ grams, int N
   __shared__ double red2[ALS_THREADS];
   const int RR = R * R;
   double xh = 0.0, inn = 0.0;
-  if (!*err) {
+  const bool bad = warp_err(err) != 0;
+  if (!bad) {
     for (int e = threadIdx.x; e < RR; e += blockDim.x) {
       double h = 1.0;
       for (int w = 0; w < N; ++w) h *= grams[(int64_t)w * RR + e];
       xh += lambda[e / R] * lambda[e % R] * h;
     }
-    for (int r = threadIdx.x; r < R; r += blockDim.x) {
-      double s = 0.0;
-      for (int b = 0; b < nblocks; ++b) s += inner_part[(int64_t)b * R + r];
-      inn += lambda[r] * s;
-      lambda_out[r] = lambda[r];
+    if (nblocks <= ALS_SERIAL_PARTIALS) {
+      for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        double v = 0.0;
+        for (int b = 0; b < nblocks; ++b) v += inner_part[(int64_t)b * R + r];
+        inn += lambda[r] * v;
+        lambda_out[r] = lambda[r];
+      }
+    } else {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int r = warp; r < R; r += nw) {
+        const double v = warp_sum_strided(inner_part + r, nblocks, R, lane);
+        if (lane == 0) {
+          inn += lambda[r] * v;
+          lambda_out[r] = lambda[r];
+        }
+      }
     }
   }
   red[threadIdx.x] = xh;
@@ -361,7 +421,7 @@ __device__ __forceinline__ void fit_body(const double* __restrict__ grams, int N
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0 && fit && !*err) {
+  if (threadIdx.x == 0 && fit && !bad) {
     const double nx = *normX2;
     double res = nx + red[0] - 2.0 * red2[0];
     if (res < 0.0) res = 0.0;
