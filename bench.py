@@ -50,7 +50,8 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="scale",
-                    choices=["scale", "batching", "serving", "precision", "five", "schemes"],
+                    choices=["scale", "batching", "serving", "precision", "five", "schemes",
+                             "lean"],
                     help="scale (default, the headline line); the others print their "
                          "own JSON line")
     ap.add_argument("--tensors", type=int, default=512, help="batching: tensor count")
@@ -252,7 +253,8 @@ def main():
     if args.workload != "scale":
         if rank == 0:  # the extra workloads run on one GPU
             {"batching": run_batching, "serving": run_serving, "precision": run_precision,
-             "five": run_precision, "schemes": run_schemes}[args.workload](args, rank, world)
+             "five": run_precision, "schemes": run_schemes,
+             "lean": run_lean}[args.workload](args, rank, world)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
@@ -405,6 +407,61 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_lean(args, rank, world):
+    """Memory-lean plans (one record copy plus per-mode positions into it)
+    against full plans (one record copy per mode) on the scale and
+    precision workloads: plan bytes, plan build time, spMTTKRP time per
+    mode (FP32 factors, default partitions) and one CP-ALS sweep."""
+    import torch
+    import synth
+    import paper_2503_18198_gb300 as spm
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name in ("scale", "precision"):
+        dims, idx, vals, R, Y = synth.preset_torch(name, device="cuda")
+        N = len(dims)
+        out[name] = {}
+        for arm, flags in (("full", 0), ("lean", spm.SPM_PLAN_LEAN)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan = spm.spmttkrp_plan(dims, idx, vals, R, flags)
+            torch.cuda.synchronize()
+            plan_ms = (time.perf_counter() - t0) * 1e3
+            outs = [torch.empty(dims[d], R, device="cuda") for d in range(N)]
+            ms = []
+            for d in range(N):
+                for _ in range(3):
+                    spm.spmttkrp_run(plan, d, Y, outs[d])
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(10):
+                    spm.spmttkrp_run(plan, d, Y, outs[d])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(round(e0.elapsed_time(e1) / 10, 4))
+            fac = [y.clone() for y in Y]
+            lam = torch.zeros(R, dtype=torch.float64, device="cuda")
+            spm.cpd_als_step(plan, fac, lam)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            spm.cpd_als_step(plan, fac, lam)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[name][arm] = {"plan_bytes": spm.spmttkrp_plan_bytes(plan), "plan_ms": plan_ms,
+                              "mttkrp_ms_per_mode": ms, "als_sweep_ms": e0.elapsed_time(e1)}
+            plan.destroy()
+        f, l = out[name]["full"], out[name]["lean"]
+        out[name]["bytes_ratio_full_over_lean"] = f["plan_bytes"] / l["plan_bytes"]
+        out[name]["mttkrp_time_ratio_lean_over_full"] = (sum(l["mttkrp_ms_per_mode"]) /
+                                                         sum(f["mttkrp_ms_per_mode"]))
+        del idx, vals, Y
+    print(json.dumps({"workload": "lean", "metric": "plan bytes and spMTTKRP ms, full vs lean",
+                      "unit": "ms", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+                      "results": out}), flush=True)
 
 
 SCHEME_SHAPES = [

@@ -96,6 +96,16 @@ typedef enum {
   ((4096 / (R)) < 16 ? 16 : ((4096 / (R)) > 128 ? 128 : (4096 / (R))))
 #define SPM_ROW_COST 16 /* extra cost of a row start, in nonzeros */
 
+/* Memory-lean plan: only the mode-0 copy holds records; every other mode
+ * keeps its order as 32-bit positions into that copy (4 bytes per nonzero
+ * instead of a 16- or 32-byte record), and its MTTKRP gathers the records in
+ * that order.  Results are bitwise those of the full plan (same nonzero
+ * order, same arithmetic).  BALANCED and SCHEME2 policies only; not for
+ * batches (SPM_ERR_UNSUPPORTED).  The paper keeps one copy per mode
+ * (Sec. III-C); this trades gather traffic for memory when N copies do not
+ * fit. */
+#define SPM_PLAN_LEAN (1u << 8)
+
 /* Number of partitions kappa.  0 (default) = SPM_PARTITIONS_PER_SM times the
  * device's SM count.  The paper assigns one partition per streaming
  * multiprocessor (Sec. III-B); on GB300 two resident waves of partition
@@ -106,7 +116,7 @@ typedef enum {
 #define SPM_KAPPA(k) (((uint32_t)(k) & 0xFFFFu) << 16)
 #define SPM_KAPPA_OF(flags) (((uint32_t)(flags) >> 16) & 0xFFFFu)
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define SPM_MAX_MODES 7
 #define SPM_MAX_RANK 256
 

@@ -7,7 +7,7 @@ a thin ctypes layer over it that takes PyTorch CUDA tensors and streams.
 """
 from .binding import (SPM_FACTOR_BF16, SPM_FACTOR_FP32, SPM_KAPPA,  # noqa: F401
                       SPM_POLICY_ADAPTIVE, SPM_POLICY_BALANCED,
-                      SPM_POLICY_SCHEME1, SPM_POLICY_SCHEME2, SPM_ROW_COST,
+                      SPM_PLAN_LEAN, SPM_POLICY_SCHEME1, SPM_POLICY_SCHEME2, SPM_ROW_COST,
                       SPM_UNITS_PER_PARTITION, Batch, Plan, Server, SpmError, cpd_als_reset,
                       cpd_als_step,
                       load, spm_batch_autotune, spm_batch_create, spm_batch_destroy, spm_batch_status,

@@ -26,6 +26,9 @@ SPM_POLICY_ADAPTIVE = 3 << 4
 SPM_ROW_COST = 16
 
 
+SPM_PLAN_LEAN = 1 << 8
+
+
 def SPM_UNITS_PER_PARTITION(R: int) -> int:
     u = 4096 // int(R)
     return 16 if u < 16 else (128 if u > 128 else u)

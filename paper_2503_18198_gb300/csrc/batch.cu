@@ -149,7 +149,8 @@ spm_status batch_add(spm_batch_s* B, spmttkrp_plan_s* p, void* const* factors, d
       start_sweeps >= max_sweeps)
     return SPM_ERR_INVALID_ARG;
   const int kc = batch_kclass(p->N, p->R);
-  if (kc == KC_NONE || (B->bf16 >= 0 && B->bf16 != (int)p->bf16)) return SPM_ERR_UNSUPPORTED;
+  if (kc == KC_NONE || p->lean || (B->bf16 >= 0 && B->bf16 != (int)p->bf16))
+    return SPM_ERR_UNSUPPORTED;
   for (int d = 0; d < p->N; ++d)
     if (p->mode[d].scheme == 1) return SPM_ERR_UNSUPPORTED;
   for (int w = 0; w < p->N; ++w)
@@ -390,7 +391,8 @@ spm_status spm_batch_create(spm_batch_t* out, int ntensors, const spmttkrp_plan_
   for (int t = 0; t < ntensors; ++t) {
     const spmttkrp_plan_s* p = plans[t];
     if (!p) return SPM_ERR_INVALID_ARG;
-    if (p->bf16 != plans[0]->bf16 || batch_kclass(p->N, p->R) == KC_NONE) return SPM_ERR_UNSUPPORTED;
+    if (p->bf16 != plans[0]->bf16 || p->lean || batch_kclass(p->N, p->R) == KC_NONE)
+      return SPM_ERR_UNSUPPORTED;
   }
   spm_batch_s* B = new (std::nothrow) spm_batch_s();
   if (!B) return SPM_ERR_OOM;

@@ -71,6 +71,14 @@ void free_plan(spmttkrp_plan_s* p) {
   delete p;
 }
 
+// Lean copy: input position of each copy position = perm0[src[k]].
+__global__ void lean_perm_kernel(const int32_t* __restrict__ perm0, const int32_t* __restrict__ src,
+                                 int64_t n, int64_t* __restrict__ out) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = perm0[src[k]];
+}
+
 __global__ void perm_to_i64_kernel(const int32_t* __restrict__ in, int64_t n,
                                    int64_t* __restrict__ out) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
@@ -117,10 +125,15 @@ spm_status spmttkrp_plan(spmttkrp_plan_t* out, int nmodes, const int64_t* dims, 
     for (int w = 0; w < nmodes; ++w)
       if (!idx[w]) return SPM_ERR_INVALID_ARG;
   }
-  const uint32_t known = SPM_FACTOR_MASK | SPM_POLICY_MASK | (0xFFFFu << 16);
+  const uint32_t known = SPM_FACTOR_MASK | SPM_POLICY_MASK | SPM_PLAN_LEAN | (0xFFFFu << 16);
   if (flags & ~known) return SPM_ERR_INVALID_ARG;
   const int policy = (int)((flags & SPM_POLICY_MASK) >> 4);
   if (policy > 3) return SPM_ERR_INVALID_ARG;
+  const bool lean = (flags & SPM_PLAN_LEAN) != 0;
+  // a lean plan keeps every copy in the P1 order (Scheme 1 reorders copies)
+  if (lean && policy != (int)(SPM_POLICY_BALANCED >> 4) && policy != (int)(SPM_POLICY_SCHEME2 >> 4))
+    return SPM_ERR_UNSUPPORTED;
+  if (lean && nmodes > 5) return SPM_ERR_UNSUPPORTED;
   int kappa = (int)SPM_KAPPA_OF(flags);
   if (kappa == 0) kappa = default_kappa();
   if (kappa < 1) return SPM_ERR_CUDA;
@@ -134,6 +147,7 @@ spm_status spmttkrp_plan(spmttkrp_plan_t* out, int nmodes, const int64_t* dims, 
   p->nnz = nnz;
   p->flags = flags;
   p->bf16 = (flags & SPM_FACTOR_MASK) == SPM_FACTOR_BF16;
+  p->lean = lean;
   p->kappa = kappa;
   p->kappa_cap = kappa;
   p->nu = SPM_UNITS_PER_PARTITION(rank);
@@ -169,7 +183,10 @@ spm_status spmttkrp_plan_permutation(spmttkrp_plan_t plan, int mode, int64_t* pe
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t n = plan->nnz;
   const int blocks = (int)std::min<int64_t>(ceil_div<int64_t>(n, 256), 152 * 16);
-  perm_to_i64_kernel<<<blocks, 256, 0, s>>>(plan->mode[mode].perm, n, perm);
+  if (plan->mode[mode].src)
+    lean_perm_kernel<<<blocks, 256, 0, s>>>(plan->mode[0].perm, plan->mode[mode].src, n, perm);
+  else
+    perm_to_i64_kernel<<<blocks, 256, 0, s>>>(plan->mode[mode].perm, n, perm);
   SPM_CUDA_TRY(cudaGetLastError());
   return SPM_OK;
 }
@@ -207,7 +224,8 @@ spm_status spmttkrp_plan_bytes_estimate(int nmodes, const int64_t* dims, int64_t
   int kappa = (int)SPM_KAPPA_OF(flags);
   if (kappa == 0) kappa = default_kappa();
   size_t tr = 0;
-  plan_bytes_estimate(nmodes, dims, nnz, rank, kappa, true, resident, &tr);
+  plan_bytes_estimate(nmodes, dims, nnz, rank, kappa, true, (flags & SPM_PLAN_LEAN) != 0, resident,
+                      &tr);
   if (transient) *transient = tr;
   return SPM_OK;
 }

@@ -59,10 +59,6 @@ __device__ __forceinline__ float4 ld_factor_v4(const void* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
 }
 
-// Bring the line holding p into L1 without a destination register.
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
 
 __device__ __forceinline__ void bf16x8_to_f32(const float4 raw, float* out) {
   const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);

@@ -14,6 +14,8 @@ MttkrpKernelFn pick_mttkrp_bf16_a(int nin, int R);
 MttkrpKernelFn pick_mttkrp_bf16_b(int nin, int R);
 MttkrpKernelFn pick_mttkrp_f32_c(int R);
 MttkrpKernelFn pick_mttkrp_bf16_c(int R);
+MttkrpKernelFn pick_mttkrp_f32_lean(int nin, int R);
+MttkrpKernelFn pick_mttkrp_bf16_lean(int nin, int R);
 
 MttkrpKernelFn pick_mttkrp(bool bf16, int nin, int R) {
   if (nin == 4) return bf16 ? pick_mttkrp_bf16_c(R) : pick_mttkrp_f32_c(R);
@@ -58,7 +60,10 @@ spm_status run_mttkrp(spmttkrp_plan_s* p, int mode, const void* const* factors, 
   const int R = p->R;
   const spm_mode_copy& c = p->mode[mode];
   MttkrpArgs a{};
-  a.rec = c.rec;
+  const bool lean = c.src != nullptr;  // lean copy: records gathered from copy 0
+  a.rec = lean ? p->mode[0].rec : c.rec;
+  a.src = c.src;
+  a.fmode = mode;
   a.woff = c.woff;
   int m = 0;
   for (int w = 0; w < p->N; ++w) {
@@ -89,7 +94,10 @@ spm_status run_mttkrp(spmttkrp_plan_s* p, int mode, const void* const* factors, 
     zero_empty_rows_kernel<<<blocks, 256, 0, s>>>(c.rowmask, a.I, R, out);
     SPM_CUDA_TRY(cudaGetLastError());
   }
-  MttkrpKernelFn fn = pick_mttkrp(p->bf16, p->N - 1, R);
+  MttkrpKernelFn fn = lean ? (p->bf16 ? pick_mttkrp_bf16_lean(p->N - 1, R)
+                                      : pick_mttkrp_f32_lean(p->N - 1, R))
+                           : pick_mttkrp(p->bf16, p->N - 1, R);
+  if (!fn) return SPM_ERR_UNSUPPORTED;
   const size_t smem = mttkrp_smem_bytes(R, record_int4s(p->N), p->nu, p->bf16 ? 2 : 4);
   SPM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // Smallest shared-memory carve-out that fits: the rest of the unified

@@ -11,23 +11,23 @@ using MttkrpKernelFn = void (*)(const MttkrpArgs);
 
 // Fast shapes: the rank is VEC * LPN * CPL with one 16-byte load per lane
 // and chunk.  Anything else uses the scalar variant (one nonzero per step).
-template <typename FT, int NIN>
+template <typename FT, int NIN, bool LEAN = false>
 MttkrpKernelFn pick_mttkrp_t(int R) {
   constexpr int RI = record_int4s(NIN > 0 ? NIN + 1 : SPM_MAX_MODES);
   constexpr int VEC = 16 / (int)sizeof(FT);
   if (R % VEC == 0) {
     switch (R / VEC) {
-      case 1: return &mttkrp_kernel<RI, NIN, FT, VEC, 1, 1>;
-      case 2: return &mttkrp_kernel<RI, NIN, FT, VEC, 2, 1>;
-      case 4: return &mttkrp_kernel<RI, NIN, FT, VEC, 4, 1>;
-      case 8: return &mttkrp_kernel<RI, NIN, FT, VEC, 8, 1>;
-      case 16: return &mttkrp_kernel<RI, NIN, FT, VEC, 16, 1>;
-      case 32: return &mttkrp_kernel<RI, NIN, FT, VEC, 32, 1>;
-      case 64: return &mttkrp_kernel<RI, NIN, FT, VEC, 32, 2>;
+      case 1: return &mttkrp_kernel<RI, NIN, FT, VEC, 1, 1, LEAN>;
+      case 2: return &mttkrp_kernel<RI, NIN, FT, VEC, 2, 1, LEAN>;
+      case 4: return &mttkrp_kernel<RI, NIN, FT, VEC, 4, 1, LEAN>;
+      case 8: return &mttkrp_kernel<RI, NIN, FT, VEC, 8, 1, LEAN>;
+      case 16: return &mttkrp_kernel<RI, NIN, FT, VEC, 16, 1, LEAN>;
+      case 32: return &mttkrp_kernel<RI, NIN, FT, VEC, 32, 1, LEAN>;
+      case 64: return &mttkrp_kernel<RI, NIN, FT, VEC, 32, 2, LEAN>;
       default: break;
     }
   }
-  return &mttkrp_kernel<RI, NIN, FT, 1, 32, 8>;
+  return &mttkrp_kernel<RI, NIN, FT, 1, 32, 8, LEAN>;
 }
 
 // The generic-N variant (six or more modes) only has the scalar shape.

@@ -41,9 +41,6 @@ namespace spm {
 #ifndef SPM_L2_HINTS
 #define SPM_L2_HINTS 0  // 1: records evict-first, factor rows evict-last in L2
 #endif
-#ifndef SPM_MT_PREFETCH
-#define SPM_MT_PREFETCH 0  // steps ahead for L1 prefetch of factor rows (0: off)
-#endif
 #ifndef SPM_MT_WARPS
 #define SPM_MT_WARPS 32
 #endif
@@ -60,7 +57,9 @@ constexpr int MT_TILE_RECS = SPM_MT_TILE;  // 16-byte records per stage tile (pe
                                            // a tile of 32-byte records holds half as many
 
 struct MttkrpArgs {
-  const int4* rec;        // copy records
+  const int4* rec;        // copy records (lean copy: the mode-0 copy's)
+  const int32_t* src;     // lean copy: position in the mode-0 copy of each copy position
+  int fmode;              // lean copy: the output mode (its index is word fmode of a record)
   const int64_t* woff;    // work-unit offsets [kappa * nu + 1]
   const void* fac[SPM_MAX_MODES - 1];  // input factors in record order
   float* out;             // I_d x R
@@ -194,7 +193,21 @@ __device__ __forceinline__ void store_vec(float* row_ptr, int R, int r0, const f
 // mttkrp_partition processes partition z of one mode copy with the whole
 // thread block (every thread must call it); it is the body of the
 // single-tensor kernel and of the batched persistent kernel.
-template <int RI, int NIN, typename FT, int VEC, int LPN, int CPL>
+// Words of a mode-0 record rearranged into the mode-d order: word d moves to
+// the front, words 0..d-1 one place back (the other modes stay ascending).
+template <int W>
+__device__ __forceinline__ void rotate_to_front(int (&w)[W], int d) {
+  int cd = w[0];
+#pragma unroll
+  for (int j = 1; j < W; ++j)
+    if (j == d) cd = w[j];
+#pragma unroll
+  for (int j = W - 1; j >= 1; --j)
+    if (j <= d) w[j] = w[j - 1];
+  w[0] = cd;
+}
+
+template <int RI, int NIN, typename FT, int VEC, int LPN, int CPL, bool LEAN = false>
 __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int z) {
   using S = Slice<FT, VEC>;
   constexpr int RAWN = S::RAWN;
@@ -228,7 +241,13 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
                                          (size_t)MT_WARPS * MT_STAGES * sizeof(uint64_t));
   int* prow = reinterpret_cast<int*>(part + (size_t)2 * NU * R);  // [2 * NU]
 
-  auto row_at = [&](int64_t k) -> int { return __ldg(&a.rec[k * RI].x); };
+  auto row_at = [&](int64_t k) -> int {
+    if constexpr (LEAN)
+      return __ldg(reinterpret_cast<const int*>(a.rec) + (int64_t)__ldg(a.src + k) * (4 * RI) +
+                   a.fmode);
+    else
+      return __ldg(&a.rec[k * RI].x);
+  };
   auto rank0 = [&](int c) -> int { return (c * LPN + sub) * VEC; };
   // Vector path with the rank fixed at compile time (R == VEC * LPN * CPL):
   // full steps are processed without per-step predication, gathers address
@@ -272,9 +291,18 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
       auto issue = [&](int t) {     // lane 0 only
         const int64_t kb = k0 + (int64_t)t * TILE;
         const int64_t cnt = (k1 - kb) < TILE ? (k1 - kb) : TILE;
-        const uint32_t bytes = (uint32_t)(cnt * 16 * RI);
         const int q = seq0 + t;
         uint64_t* bar = &bars[q % MT_STAGES];
+        if constexpr (LEAN) {
+          // the tile's positions into the mode-0 copy, from the 16-byte
+          // boundary at or below kb (the position array is padded at its end)
+          const int64_t al = kb & ~(int64_t)3;
+          const uint32_t lbytes = (uint32_t)((((kb - al) + cnt) * 4 + 15) & ~(int64_t)15);
+          mbar_arrive_expect_tx(bar, lbytes);
+          bulk_g2s(stages + (q % MT_STAGES) * tile_bytes, a.src + al, lbytes, bar);
+          return;
+        }
+        const uint32_t bytes = (uint32_t)(cnt * 16 * RI);
         mbar_arrive_expect_tx(bar, bytes);
 #if SPM_L2_HINTS
         bulk_g2s_hint(stages + (q % MT_STAGES) * tile_bytes, a.rec + kb * RI, bytes, bar,
@@ -368,16 +396,42 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
           if (lane == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
           break;
         }
-        const int4* recs =
-            reinterpret_cast<const int4*>(stages + ((seq0 + t) % MT_STAGES) * tile_bytes);
+        const unsigned char* stage_t = stages + ((seq0 + t) % MT_STAGES) * tile_bytes;
+        const int4* recs = reinterpret_cast<const int4*>(stage_t);
+        // lean copy: the stage holds positions into the mode-0 copy
+        const int* srcs = reinterpret_cast<const int*>(stage_t) +
+                          (LEAN ? (int)((k0 + (int64_t)t * TILE) & 3) : 0);
+        auto load_rec = [&](int pos, int (&wv)[W]) {
+          if constexpr (LEAN) {
+            const int4* r = a.rec + (int64_t)srcs[pos] * RI;
+#pragma unroll
+            for (int qq = 0; qq < RI; ++qq) {
+              const int4 v4 = __ldg(r + qq);
+              wv[4 * qq] = v4.x; wv[4 * qq + 1] = v4.y; wv[4 * qq + 2] = v4.z; wv[4 * qq + 3] = v4.w;
+            }
+            rotate_to_front<W>(wv, a.fmode);
+          } else {
+#pragma unroll
+            for (int qq = 0; qq < RI; ++qq) {
+              const int4 v4 = recs[pos * RI + qq];
+              wv[4 * qq] = v4.x; wv[4 * qq + 1] = v4.y; wv[4 * qq + 2] = v4.z; wv[4 * qq + 3] = v4.w;
+            }
+          }
+        };
+        auto tile_row = [&](int pos) -> int {
+          if constexpr (LEAN)
+            return __ldg(reinterpret_cast<const int*>(a.rec) + (int64_t)srcs[pos] * (4 * RI) +
+                         a.fmode);
+          else
+            return recs[pos * RI].x;
+        };
         const int n = (lenw - t * TILE) < TILE ? (lenw - t * TILE) : TILE;
         const int nst = (n + G - 1) / G;
-        const bool pure = recs[0].x == cur && recs[(n - 1) * RI].x == cur;
+        const bool pure = tile_row(0) == cur && tile_row(n - 1) == cur;
         int j_fast = 0;
         if constexpr (FAST) {
           // full steps (a record in every slot), U at a time
           const int nb = ((n / G) / U) * U;
-          const unsigned char* rb = reinterpret_cast<const unsigned char*>(recs) + slot * 16 * RI;
 #if SPM_MT_REUSE
           int last0 = -1;               // index of the first input mode's row held in y0prev
           uint32_t y0prev[CPL][RAWN];
@@ -393,13 +447,7 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
             int w[U][W];
             uint32_t y[U][NINF][CPL][RAWN];
 #pragma unroll
-            for (int uu = 0; uu < U; ++uu)
-#pragma unroll
-              for (int qq = 0; qq < RI; ++qq) {
-                const int4 v4 = *reinterpret_cast<const int4*>(rb + ((j + uu) * G * RI + qq) * 16);
-                w[uu][4 * qq] = v4.x; w[uu][4 * qq + 1] = v4.y;
-                w[uu][4 * qq + 2] = v4.z; w[uu][4 * qq + 3] = v4.w;
-              }
+            for (int uu = 0; uu < U; ++uu) load_rec((j + uu) * G + slot, w[uu]);
 #if SPM_MT_REUSE
             bool fresh0[U];
             {
@@ -511,27 +559,6 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
           j_fast = nb;
         }
         for (int j = j_fast; j < nst; j += U) {
-#if SPM_MT_PREFETCH > 0
-          // Pull the factor rows of the steps SPM_MT_PREFETCH ahead into L1
-          // (no registers held while they are in flight).
-          if (pure) {
-#pragma unroll
-            for (int uu = 0; uu < U; ++uu) {
-              const int pos = (j + uu + SPM_MT_PREFETCH) * G + slot;
-              if (pos < n) {
-                const int4 r4 = recs[pos * RI];
-                const int cw[3] = {r4.y, r4.z, r4.w};
-#pragma unroll
-                for (int m = 0; m < NPIPE && m < 3; ++m)
-                  if (m < nin) {
-#pragma unroll
-                    for (int c = 0; c < CPL; ++c)
-                      prefetch_l1(static_cast<const FT*>(a.fac[m]) + (int64_t)cw[m] * R + rank0(c));
-                  }
-              }
-            }
-          }
-#endif
           int w[U][W];
           bool valid[U];
           uint32_t y[U][NPIPE][CPL][RAWN];
@@ -541,14 +568,7 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
             valid[uu] = (j + uu) < nst && pos < n;
 #pragma unroll
             for (int qq = 0; qq < W; ++qq) w[uu][qq] = 0;
-            if (valid[uu]) {
-#pragma unroll
-              for (int qq = 0; qq < RI; ++qq) {
-                const int4 v4 = recs[pos * RI + qq];
-                w[uu][4 * qq] = v4.x; w[uu][4 * qq + 1] = v4.y;
-                w[uu][4 * qq + 2] = v4.z; w[uu][4 * qq + 3] = v4.w;
-              }
-            }
+            if (valid[uu]) load_rec(pos, w[uu]);
           }
 #pragma unroll
           for (int uu = 0; uu < U; ++uu)
@@ -776,9 +796,9 @@ __device__ __forceinline__ void zero_empty_rows_body(const uint32_t* __restrict_
   }
 }
 
-template <int RI, int NIN, typename FT, int VEC, int LPN, int CPL>
+template <int RI, int NIN, typename FT, int VEC, int LPN, int CPL, bool LEAN = false>
 __global__ void __launch_bounds__(MT_THREADS, 1) mttkrp_kernel(const MttkrpArgs a) {
-  mttkrp_partition<RI, NIN, FT, VEC, LPN, CPL>(a, blockIdx.x);
+  mttkrp_partition<RI, NIN, FT, VEC, LPN, CPL, LEAN>(a, blockIdx.x);
 }
 
 }  // namespace spm

@@ -465,16 +465,17 @@ __global__ void partitions_from_units_kernel(const int64_t* __restrict__ woff, i
     off[z] = woff[(int64_t)z * units];
 }
 
-// Row starts per tile of RS_TILE copy positions.
-template <int RI>
+// Row starts per tile of RS_TILE copy positions.  The row of copy position k
+// is rows[k * stride] (a copy's records, or a gathered key array).
 __global__ void __launch_bounds__(RS_THREADS)
-    head_count_kernel(const int4* __restrict__ rec, int64_t n, uint32_t* __restrict__ bsum) {
+    head_count_kernel(const int* __restrict__ rows, int64_t stride, int64_t n,
+                      uint32_t* __restrict__ bsum) {
   __shared__ uint32_t red[RS_THREADS];
   const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)threadIdx.x * RS_ITEMS;
   uint32_t c = 0;
   for (int i = 0; i < RS_ITEMS; ++i) {
     const int64_t k = base + i;
-    if (k < n) c += (k == 0 || rec[k * RI].x != rec[(k - 1) * RI].x) ? 1u : 0u;
+    if (k < n) c += (k == 0 || rows[k * stride] != rows[(k - 1) * stride]) ? 1u : 0u;
   }
   red[threadIdx.x] = c;
   __syncthreads();
@@ -486,16 +487,15 @@ __global__ void __launch_bounds__(RS_THREADS)
 }
 
 // heads_before[k] = number of row starts at positions < k (bsum scanned).
-template <int RI>
 __global__ void __launch_bounds__(RS_THREADS)
-    head_prefix_kernel(const int4* __restrict__ rec, int64_t n, const uint32_t* __restrict__ bexcl,
-                       uint32_t* __restrict__ before) {
+    head_prefix_kernel(const int* __restrict__ rows, int64_t stride, int64_t n,
+                       const uint32_t* __restrict__ bexcl, uint32_t* __restrict__ before) {
   __shared__ uint32_t sc[RS_THREADS];
   const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)threadIdx.x * RS_ITEMS;
   uint32_t c = 0;
   for (int i = 0; i < RS_ITEMS; ++i) {
     const int64_t k = base + i;
-    if (k < n) c += (k == 0 || rec[k * RI].x != rec[(k - 1) * RI].x) ? 1u : 0u;
+    if (k < n) c += (k == 0 || rows[k * stride] != rows[(k - 1) * stride]) ? 1u : 0u;
   }
   sc[threadIdx.x] = c;
   __syncthreads();
@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(RS_THREADS)
     const int64_t k = base + i;
     if (k < n) {
       before[k] = run;
-      run += (k == 0 || rec[k * RI].x != rec[(k - 1) * RI].x) ? 1u : 0u;
+      run += (k == 0 || rows[k * stride] != rows[(k - 1) * stride]) ? 1u : 0u;
     }
   }
 }
@@ -534,16 +534,24 @@ __global__ void balanced_units_kernel(const uint32_t* __restrict__ before,
   }
 }
 
-// Bitmap of non-empty output rows of a copy (sorted or partition-ordered:
-// every nonzero sets its row's bit).
-template <int RI>
-__global__ void row_mask_kernel(const int4* __restrict__ rec, int64_t n,
+// Bitmap of non-empty output rows of a copy (rows[k * stride] is the row of
+// copy position k; every nonzero sets its row's bit).
+__global__ void row_mask_kernel(const int* __restrict__ rows, int64_t stride, int64_t n,
                                 uint32_t* __restrict__ mask) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const int r = rec[k * RI].x;
-    if (k == 0 || rec[(k - 1) * RI].x != r) atomicOr(&mask[r >> 5], 1u << (r & 31));
+    const int r = rows[k * stride];
+    if (k == 0 || rows[(k - 1) * stride] != r) atomicOr(&mask[r >> 5], 1u << (r & 31));
   }
+}
+
+// Lean copy d: row of each copy position, gathered from copy 0 (word d of
+// the copy-0 record is c_d).
+__global__ void gather_rows_kernel(const int* __restrict__ rec0, int64_t words, const int32_t* __restrict__ src,
+                                   int d, int64_t n, int* __restrict__ rows) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    rows[k] = rec0[(int64_t)src[k] * words + d];
 }
 
 __global__ void popc_kernel(const uint32_t* __restrict__ mask, int64_t words,
@@ -569,13 +577,28 @@ int bits_for(int64_t dim) {
 
 constexpr int NORM_BLOCKS = 1024;
 
+// The rows of copy d in copy order as (pointer, stride): the copy's records,
+// or for a lean copy a key array gathered into `scratch` (>= nnz ints).
+const int* copy_rows(spmttkrp_plan_s* p, int d, int* scratch, int64_t* stride, cudaStream_t s) {
+  const int RI = record_int4s(p->N);
+  if (!p->lean || d == 0) {
+    *stride = 4 * RI;
+    return reinterpret_cast<const int*>(p->mode[d].rec);
+  }
+  const int64_t n = p->nnz;
+  gather_rows_kernel<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const int*>(p->mode[0].rec),
+                                                     4 * RI, p->mode[d].src, d, n, scratch);
+  *stride = 1;
+  return scratch;
+}
+
 // P2 for a copy under the cost-balanced policy (scheme 0) or Scheme 2, and
 // for an empty tensor under any policy: partition offsets off[0..kappa] and
-// work-unit offsets woff[0..kappa*nu].  Scratch: hist >= ceil(nnz/RS_TILE)
-// words, dtot >= 1 word, before >= nnz words.
-template <int RI>
-void partition_copy(spmttkrp_plan_s* p, int d, uint32_t* hist, uint32_t* dtot, uint32_t* before,
-                    cudaStream_t s) {
+// work-unit offsets woff[0..kappa*nu].  rows/stride: the copy's rows in copy
+// order.  Scratch: hist >= ceil(nnz/RS_TILE) words, dtot >= 1 word,
+// before >= nnz words.
+void partition_copy(spmttkrp_plan_s* p, int d, const int* rows, int64_t stride, uint32_t* hist,
+                    uint32_t* dtot, uint32_t* before, cudaStream_t s) {
   const int T = 256;
   const int64_t n = p->nnz;
   const int units = p->nu;
@@ -584,9 +607,9 @@ void partition_copy(spmttkrp_plan_s* p, int d, uint32_t* hist, uint32_t* dtot, u
   if (c.scheme == 0 && n > 0) {
     // cost-balanced work units over the copy order
     const int nb = (int)ceil_div<int64_t>(n, RS_TILE);
-    head_count_kernel<RI><<<nb, RS_THREADS, 0, s>>>(c.rec, n, hist);
+    head_count_kernel<<<nb, RS_THREADS, 0, s>>>(rows, stride, n, hist);
     rs_scan_rows_kernel<<<1, 1024, 0, s>>>(hist, nb, dtot);
-    head_prefix_kernel<RI><<<nb, RS_THREADS, 0, s>>>(c.rec, n, hist, before);
+    head_prefix_kernel<<<nb, RS_THREADS, 0, s>>>(rows, stride, n, hist, before);
     balanced_units_kernel<<<grid_for(P + 1, T), T, 0, s>>>(before, dtot, n, P, SPM_ROW_COST,
                                                           c.woff);
     partitions_from_units_kernel<<<grid_for(p->kappa + 1, T), T, 0, s>>>(c.woff, p->kappa,
@@ -634,10 +657,15 @@ spm_status build_copies_t(spmttkrp_plan_s* p, const int32_t* const* idx_in, cons
   spm_status st = SPM_OK;
   if (herr & DEV_ERR_INDEX) st = SPM_ERR_INDEX_OUT_OF_RANGE;
 
-  // Allocate the copies.
+  // Allocate the copies (a lean copy: positions into copy 0, padded by 16
+  // bytes so that 16-byte-aligned bulk copies of any range stay inside).
   for (int d = 0; d < N && st == SPM_OK; ++d) {
-    st = plan_alloc(p, (void**)&p->mode[d].rec, sizeof(int4) * RI * (size_t)nn + 256);
-    if (st == SPM_OK) st = plan_alloc(p, (void**)&p->mode[d].perm, sizeof(int32_t) * (size_t)nn);
+    if (p->lean && d > 0) {
+      st = plan_alloc(p, (void**)&p->mode[d].src, sizeof(int32_t) * (size_t)nn + 16);
+    } else {
+      st = plan_alloc(p, (void**)&p->mode[d].rec, sizeof(int4) * RI * (size_t)nn + 256);
+      if (st == SPM_OK) st = plan_alloc(p, (void**)&p->mode[d].perm, sizeof(int32_t) * (size_t)nn);
+    }
     if (st == SPM_OK)
       st = plan_alloc(p, (void**)&p->mode[d].off, sizeof(int64_t) * (size_t)(p->kappa + 1));
     if (st == SPM_OK)
@@ -702,8 +730,12 @@ spm_status build_copies_t(spmttkrp_plan_s* p, const int32_t* const* idx_in, cons
       iota_kernel<<<G, T, 0, s>>>(ra, n);
       st = radix_sort_pairs<uint32_t>(ka32, ra, kb32, rb, n, bits[d], sc, s);
       if (st != SPM_OK) break;
-      records_from_copy0_kernel<RI><<<G, T, 0, s>>>(p->mode[0].rec, p->mode[0].perm, ra, N, d, n,
-                                                     p->mode[d].rec, p->mode[d].perm);
+      if (p->lean)
+        SPM_CUDA_TRY(cudaMemcpyAsync(p->mode[d].src, ra, sizeof(int32_t) * n,
+                                     cudaMemcpyDeviceToDevice, s));
+      else
+        records_from_copy0_kernel<RI><<<G, T, 0, s>>>(p->mode[0].rec, p->mode[0].perm, ra, N, d,
+                                                       n, p->mode[d].rec, p->mode[d].perm);
     }
   } else if (st == SPM_OK) {
     SPM_CUDA_TRY(cudaMemsetAsync(p->normX2, 0, sizeof(double), s));
@@ -720,7 +752,9 @@ spm_status build_copies_t(spmttkrp_plan_s* p, const int32_t* const* idx_in, cons
     if (p->policy == (int)(SPM_POLICY_ADAPTIVE >> 4)) scheme = p->dims[d] >= p->kappa ? 1 : 2;
     c.scheme = scheme;
     if (scheme != 1 || n == 0) {
-      partition_copy<RI>(p, d, sc.hist, sc.dtot, reinterpret_cast<uint32_t*>(va), s);
+      int64_t stride = 0;
+      const int* rows = n > 0 ? copy_rows(p, d, reinterpret_cast<int*>(k64b), &stride, s) : nullptr;
+      partition_copy(p, d, rows, stride, sc.hist, sc.dtot, reinterpret_cast<uint32_t*>(va), s);
       continue;
     }
     // Scheme 1: degree-ordered cyclic deal of the rows, copy ordered by partition.
@@ -775,7 +809,11 @@ spm_status build_copies_t(spmttkrp_plan_s* p, const int32_t* const* idx_in, cons
     for (int d = 0; d < N; ++d) {
       const int64_t words = (p->dims[d] + 31) / 32;
       SPM_CUDA_TRY(cudaMemsetAsync(p->mode[d].rowmask, 0, sizeof(uint32_t) * words, s));
-      if (n > 0) row_mask_kernel<RI><<<G, T, 0, s>>>(p->mode[d].rec, n, p->mode[d].rowmask);
+      if (n > 0) {
+        int64_t stride = 0;
+        const int* rows = copy_rows(p, d, reinterpret_cast<int*>(k64b), &stride, s);
+        row_mask_kernel<<<G, T, 0, s>>>(rows, stride, n, p->mode[d].rowmask);
+      }
       popc_kernel<<<grid_for(words, T), T, 0, s>>>(p->mode[d].rowmask, words, d_cnt + d);
     }
     SPM_CUDA_TRY(cudaMemcpyAsync(h_cnt, d_cnt, sizeof(unsigned long long) * SPM_MAX_MODES,
@@ -798,7 +836,7 @@ spm_status build_copies_t(spmttkrp_plan_s* p, const int32_t* const* idx_in, cons
 }  // namespace
 
 void plan_bytes_estimate(int N, const int64_t* dims, int64_t nnz, int R, int kappa, bool als,
-                         size_t* resident, size_t* transient) {
+                         bool lean, size_t* resident, size_t* transient) {
   // mirrors the plan_alloc calls of spmttkrp_plan, build_copies and
   // ensure_als_state (each allocation of 0 bytes counts 16)
   const int RI = record_int4s(N);
@@ -810,8 +848,12 @@ void plan_bytes_estimate(int N, const int64_t* dims, int64_t nnz, int R, int kap
   b += sizeof(float) * 2 * (size_t)kappa * R + sizeof(int) * 4 * (size_t)kappa;
   b += sizeof(double) * NORM_BLOCKS;
   for (int d = 0; d < N; ++d) {
-    b += sizeof(int4) * RI * (size_t)nn + 256;
-    b += sizeof(int32_t) * (size_t)nn;
+    if (lean && d > 0) {
+      b += sizeof(int32_t) * (size_t)nn + 16;
+    } else {
+      b += sizeof(int4) * RI * (size_t)nn + 256;
+      b += sizeof(int32_t) * (size_t)nn;
+    }
     b += sizeof(int64_t) * (size_t)(kappa + 1);
     b += sizeof(int64_t) * ((size_t)kappa * nu + 1);
     b += sizeof(uint32_t) * (size_t)((dims[d] + 31) / 32);
@@ -853,17 +895,21 @@ spm_status plan_repartition(spmttkrp_plan_s* p, int kappa, cudaStream_t s) {
   const int64_t n = p->nnz;
   const int64_t nn = n > 0 ? n : 1;
   uint32_t *hist = nullptr, *dtot = nullptr, *before = nullptr;
+  int* rows_tmp = nullptr;
   SPM_CUDA_TRY(cudaMallocAsync((void**)&hist, sizeof(uint32_t) * ceil_div<int64_t>(nn, RS_TILE), s));
   SPM_CUDA_TRY(cudaMallocAsync((void**)&dtot, sizeof(uint32_t), s));
   SPM_CUDA_TRY(cudaMallocAsync((void**)&before, sizeof(uint32_t) * nn, s));
+  if (p->lean) SPM_CUDA_TRY(cudaMallocAsync((void**)&rows_tmp, sizeof(int) * nn, s));
   for (int d = 0; d < p->N; ++d) {
-    if (record_int4s(p->N) == 1) partition_copy<1>(p, d, hist, dtot, before, s);
-    else partition_copy<2>(p, d, hist, dtot, before, s);
+    int64_t stride = 0;
+    const int* rows = n > 0 ? copy_rows(p, d, rows_tmp, &stride, s) : nullptr;
+    partition_copy(p, d, rows, stride, hist, dtot, before, s);
   }
   SPM_CUDA_TRY(cudaGetLastError());
   SPM_CUDA_TRY(cudaFreeAsync(hist, s));
   SPM_CUDA_TRY(cudaFreeAsync(dtot, s));
   SPM_CUDA_TRY(cudaFreeAsync(before, s));
+  if (rows_tmp) SPM_CUDA_TRY(cudaFreeAsync(rows_tmp, s));
   return SPM_OK;
 }
 

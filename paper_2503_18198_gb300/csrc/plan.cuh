@@ -5,8 +5,9 @@
 #include "common.cuh"
 
 struct spm_mode_copy {
-  int4* rec = nullptr;       // records, record_int4s(N) int4 per nonzero
-  int32_t* perm = nullptr;   // input position of each copy position
+  int4* rec = nullptr;       // records, record_int4s(N) int4 per nonzero (null: lean copy)
+  int32_t* perm = nullptr;   // input position of each copy position (null: lean copy)
+  int32_t* src = nullptr;    // lean copy: position in copy 0 of each copy position
   int64_t* off = nullptr;    // device int64[kappa+1] partition offsets
   int64_t* woff = nullptr;   // device int64[kappa*nu+1] work-unit offsets
   uint32_t* rowmask = nullptr;  // bit i set: output row i has a nonzero
@@ -37,6 +38,7 @@ struct spmttkrp_plan_s {
   int64_t nnz = 0;
   uint32_t flags = 0;
   bool bf16 = false;
+  bool lean = false;  // SPM_PLAN_LEAN: copies 1..N-1 are positions into copy 0
   int kappa = 0;
   int kappa_cap = 0;  // partitions the off/woff/cta arrays are sized for
   int nu = 0;      // work units per partition
@@ -70,7 +72,7 @@ spm_status plan_realloc(spmttkrp_plan_s* p, void** ptr, size_t bytes);
 // with `als` the CP-ALS state) and the most its build adds for a while
 // (transient scratch), for the given shape.
 void plan_bytes_estimate(int N, const int64_t* dims, int64_t nnz, int R, int kappa, bool als,
-                         size_t* resident, size_t* transient);
+                         bool lean, size_t* resident, size_t* transient);
 
 // P2 again for a new partition count (cost-balanced and Scheme 2 policies).
 spm_status plan_repartition(spmttkrp_plan_s* p, int kappa, cudaStream_t s);

@@ -225,7 +225,7 @@ spm_status spm_server_submit(spm_server_t S, const spm_job_desc* d, int64_t* job
         1, std::min<int64_t>(0xFFFF, ceil_div<int64_t>(std::max<int64_t>(1, d->nnz),
                                                        S->nnz_per_partition)));
   j->plan_flags = (S->flags & SPM_FACTOR_MASK) | SPM_KAPPA(kappa);
-  plan_bytes_estimate(N, j->dims, j->nnz, j->R, kappa, true, &j->resident, &j->transient);
+  plan_bytes_estimate(N, j->dims, j->nnz, j->R, kappa, true, false, &j->resident, &j->transient);
   j->t_submit = now_ms();
   S->queue.push_back(j);
   S->jobs[j->id] = j;
