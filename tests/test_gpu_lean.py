@@ -132,3 +132,30 @@ def test_lean_repartition_autotune_and_restrictions():
     with pytest.raises(spm.SpmError) as e:
         spm.spm_batch_create([lean], [Y], lam, fits)
     assert e.value.status == 7
+
+
+@pytest.mark.parametrize("nnz,dup", [(0, False), (1, False), (3000, True)])
+def test_lean_edge_cases(nnz, dup):
+    """Empty and one-nonzero tensors, and repeated coordinates (summed)."""
+    dims = (40, 30, 20)
+    if nnz == 0:
+        idx = [np.zeros(0, np.int32) for _ in dims]
+        vals = np.zeros(0, np.float32)
+    else:
+        _, idx, vals = synth.coo_random(dims, nnz, seed=11, duplicates=dup)
+    didx = [torch.as_tensor(c).cuda() for c in idx]
+    dvals = torch.as_tensor(vals).cuda()
+    full = spm.spmttkrp_plan(dims, didx, dvals, 16)
+    lean = spm.spmttkrp_plan(dims, didx, dvals, 16, spm.SPM_PLAN_LEAN)
+    Y = [torch.as_tensor(f).cuda() for f in synth.factors(dims, 16, seed=11)]
+    for d in range(3):
+        of = torch.full((dims[d], 16), float("nan"), device="cuda")
+        ol = torch.full((dims[d], 16), float("nan"), device="cuda")
+        spm.spmttkrp_run(full, d, Y, of)
+        spm.spmttkrp_run(lean, d, Y, ol)
+        assert torch.equal(of, ol)
+        if nnz:
+            ref = oracle.mttkrp(dims, idx, vals, [y.double().cpu().numpy() for y in Y], d)
+            assert np.linalg.norm(ol.double().cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-5
+        else:
+            assert torch.count_nonzero(ol) == 0
