@@ -237,6 +237,23 @@ spm_status spmttkrp_run_noalloc(int nmodes, const int64_t *dims, int64_t nnz,
 
 /* ---- CPD-ALS --------------------------------------------------------------- */
 
+/* spMTTKRP along every mode 0..N-1 from and to host memory:
+ *  host_factors  host array of N host pointers to the factors (I_w x R,
+ *                FP32 or BF16 per the plan, row-major);
+ *  host_out      host array of N host pointers to the outputs (I_d x R FP32).
+ * The factors are copied to device staging buffers owned by the plan
+ * (allocated on the first call), factors 1..N-1 first so that mode 0 starts
+ * while factor 0 is still in flight; each output is copied back on a side
+ * stream while the next mode computes.  Launch-only: the call returns once
+ * everything is queued, and work queued on `stream` afterwards (or a
+ * synchronisation of it) sees all copies complete.  With pinned host memory
+ * the copies are asynchronous and overlap; with pageable memory they are
+ * correct but staged by the driver.  The host buffers must stay valid until
+ * then.  The paper runs its kernel on device-resident data; this is the
+ * host-facing form of the same computation. */
+spm_status spmttkrp_run_all_host(spmttkrp_plan_t plan, const void *const *host_factors,
+                                 float *const *host_out, void *stream);
+
 /* One CP-ALS sweep over modes 0..N-1 in order (Sec. II-A5), Gauss-Seidel:
  * for each d,
  *   M      = spMTTKRP_d(factors)                     (the plan's kernels)

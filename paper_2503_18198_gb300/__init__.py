@@ -19,5 +19,5 @@ from .binding import (SPM_FACTOR_BF16, SPM_FACTOR_FP32, SPM_KAPPA,  # noqa: F401
                       spmttkrp_plan_autotune, spmttkrp_plan_repartition,
                       spmttkrp_plan_scheme,
                       spmttkrp_plan_status,
-                      spmttkrp_plan_work_units, spmttkrp_run,
+                      spmttkrp_plan_work_units, spmttkrp_run, spmttkrp_run_all_host,
                       spmttkrp_run_noalloc)

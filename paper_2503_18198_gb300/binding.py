@@ -67,7 +67,8 @@ SYMBOLS = ("spmttkrp_plan", "spmttkrp_plan_bytes", "spmttkrp_plan_permutation",
            "spmttkrp_plan_bytes_estimate", "spm_server_create", "spm_server_submit",
            "spm_server_step", "spm_server_job", "spm_server_result", "spm_server_usage",
            "spm_server_destroy", "spm_selftest_wait_timeout", "spm_inject_alloc_failure",
-           "cpd_als_reset", "spm_server_snapshot", "spm_server_resume")
+           "cpd_als_reset", "spm_server_snapshot", "spm_server_resume",
+           "spmttkrp_run_all_host")
 
 
 def library_path() -> str:
@@ -145,6 +146,8 @@ def load(build_if_missing: bool = False):
     lib.spm_selftest_wait_timeout.restype = i32
     lib.spm_inject_alloc_failure.argtypes = [i32]
     lib.spm_inject_alloc_failure.restype = None
+    lib.spmttkrp_run_all_host.argtypes = [P, P, P, P]
+    lib.spmttkrp_run_all_host.restype = i32
     lib.cpd_als_reset.argtypes = [P]
     lib.cpd_als_reset.restype = i32
     lib.spm_server_snapshot.argtypes = [P, i64, P, P, P, P, P]
@@ -298,6 +301,14 @@ def spmttkrp_run(plan: Plan, mode: int, factors, out, stream=None):
                                ctypes.c_void_p(out.data_ptr()), _stream(stream)),
            "spmttkrp_run")
     return out
+
+
+def spmttkrp_run_all_host(plan: Plan, host_factors, host_outs, stream=None):
+    """MTTKRP along every mode from host (CPU) tensors into host tensors;
+    launch-only (synchronise the stream before reading host_outs)."""
+    _check(load().spmttkrp_run_all_host(plan.handle, _ptrs(list(host_factors)),
+                                        _ptrs(list(host_outs)), _stream(stream)),
+           "spmttkrp_run_all_host")
 
 
 def cpd_als_step(plan: Plan, factors, lam, fit=None, stream=None):

@@ -66,6 +66,10 @@ namespace {
 
 void free_plan(spmttkrp_plan_s* p) {
   if (!p) return;
+  for (cudaEvent_t e : p->ev)
+    if (e) cudaEventDestroy(e);
+  if (p->copy_in) cudaStreamDestroy(p->copy_in);
+  if (p->copy_out) cudaStreamDestroy(p->copy_out);
   for (int i = 0; i < p->nallocs; ++i) cudaFree(p->allocs[i]);
   (void)cudaGetLastError();
   delete p;
@@ -316,6 +320,55 @@ spm_status cpd_als_step(spmttkrp_plan_t plan, void* const* factors, double* lamb
 spm_status cpd_als_reset(spmttkrp_plan_t plan) {
   if (!plan) return SPM_ERR_INVALID_ARG;
   plan->als.ready = false;
+  return SPM_OK;
+}
+
+spm_status spmttkrp_run_all_host(spmttkrp_plan_t p, const void* const* host_factors,
+                                 float* const* host_out, void* stream) {
+  NvtxScope nv("spmttkrp_run_all_host");
+  if (!p || !host_factors || !host_out) return SPM_ERR_INVALID_ARG;
+  const int N = p->N, R = p->R;
+  for (int w = 0; w < N; ++w)
+    if (!host_factors[w] || !host_out[w]) return SPM_ERR_INVALID_ARG;
+  const size_t sf = p->bf16 ? 2 : 4;
+  if (!p->h_fac[0]) {  // first call: staging buffers, side streams, events
+    for (int w = 0; w < N; ++w) {
+      SPM_TRY(plan_alloc(p, &p->h_fac[w], sf * (size_t)p->dims[w] * R));
+      SPM_TRY(plan_alloc(p, (void**)&p->h_out[w], sizeof(float) * (size_t)p->dims[w] * R));
+    }
+    SPM_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_in, cudaStreamNonBlocking));
+    SPM_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_out, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : p->ev) SPM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t* ev_in = p->ev;                   // [N] factor w on the device
+  cudaEvent_t* ev_done = p->ev + SPM_MAX_MODES;  // [N] output d computed
+  cudaEvent_t ev_start = p->ev[2 * SPM_MAX_MODES];
+  cudaEvent_t ev_outs = p->ev[2 * SPM_MAX_MODES + 1];
+  // copies start after the caller's earlier work on `stream`
+  SPM_CUDA_TRY(cudaEventRecord(ev_start, s));
+  SPM_CUDA_TRY(cudaStreamWaitEvent(p->copy_in, ev_start, 0));
+  SPM_CUDA_TRY(cudaStreamWaitEvent(p->copy_out, ev_start, 0));
+  // factors 1..N-1 first (mode 0 needs exactly those), factor 0 last
+  for (int k = 1; k <= N; ++k) {
+    const int w = k % N;
+    SPM_CUDA_TRY(cudaMemcpyAsync(p->h_fac[w], host_factors[w], sf * (size_t)p->dims[w] * R,
+                                 cudaMemcpyHostToDevice, p->copy_in));
+    SPM_CUDA_TRY(cudaEventRecord(ev_in[w], p->copy_in));
+  }
+  for (int d = 0; d < N; ++d) {
+    for (int w = 0; w < N; ++w)
+      if (w != d) SPM_CUDA_TRY(cudaStreamWaitEvent(s, ev_in[w], 0));
+    SPM_TRY(run_mttkrp(p, d, p->h_fac, p->h_out[d], s));
+    SPM_CUDA_TRY(cudaEventRecord(ev_done[d], s));
+    // output d goes back while mode d + 1 computes
+    SPM_CUDA_TRY(cudaStreamWaitEvent(p->copy_out, ev_done[d], 0));
+    SPM_CUDA_TRY(cudaMemcpyAsync(host_out[d], p->h_out[d], sizeof(float) * (size_t)p->dims[d] * R,
+                                 cudaMemcpyDeviceToHost, p->copy_out));
+  }
+  // work queued on `stream` after this call sees every copy done
+  SPM_CUDA_TRY(cudaEventRecord(ev_outs, p->copy_out));
+  SPM_CUDA_TRY(cudaStreamWaitEvent(s, ev_outs, 0));
   return SPM_OK;
 }
 

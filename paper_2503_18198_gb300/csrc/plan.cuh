@@ -52,6 +52,12 @@ struct spmttkrp_plan_s {
   double* normX2 = nullptr;    // |X|_F^2 (duplicates summed)
   double* norm_part = nullptr; // partials for normX2
   spm_als_state als;
+  // host-buffer entry point: device staging of factors and outputs, and the
+  // side streams / events that overlap its copies with the modes' kernels
+  void* h_fac[SPM_MAX_MODES] = {};
+  float* h_out[SPM_MAX_MODES] = {};
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaEvent_t ev[2 * SPM_MAX_MODES + 2] = {};
   size_t bytes = 0;
   // allocation bookkeeping
   void* allocs[64] = {};
