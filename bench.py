@@ -903,7 +903,7 @@ def run_precision(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-KERNEL_SOURCES = ("mttkrp_kernel.cuh", "mttkrp.cu", "mttkrp_inst.cuh", "common.cuh", "plan.cuh")
+KERNEL_SOURCES = ("mttkrp_kernel.cuh", "mttkrp.cu", "mttkrp_inst.cuh", "common.cuh")
 
 
 def kernel_digest():

@@ -25,8 +25,8 @@ namespace {
 template <typename FT, int GT>
 __global__ void __launch_bounds__(ALS_THREADS)
     gram_partial_kernel(const FT* __restrict__ Y, int64_t I, int R, int64_t rows_per_block,
-                        double* __restrict__ part) {
-  gram_partial_body<FT, GT>(Y, I, R, rows_per_block, part, blockIdx.x);
+                        double* __restrict__ part, const uint32_t* __restrict__ mask) {
+  gram_partial_body<FT, GT>(Y, I, R, rows_per_block, part, blockIdx.x, mask);
 }
 
 __global__ void gram_reduce_kernel(const double* __restrict__ part, int nblocks, int R,
@@ -44,8 +44,8 @@ template <int RPL>
 __global__ void __launch_bounds__(ALS_THREADS)
     solve_kernel(const float* __restrict__ M, const float* __restrict__ winv, int64_t I, int R,
                  float* __restrict__ Z, double* __restrict__ colsq_part,
-                 const int* __restrict__ err) {
-  solve_body<RPL>(M, winv, I, R, Z, colsq_part, err, blockIdx.x, gridDim.x);
+                 const int* __restrict__ err, const uint32_t* __restrict__ mask) {
+  solve_body<RPL>(M, winv, I, R, Z, colsq_part, err, blockIdx.x, gridDim.x, mask);
 }
 
 __global__ void lambda_kernel(const double* __restrict__ colsq_part, int nblocks, int R,
@@ -57,8 +57,8 @@ template <typename FT>
 __global__ void __launch_bounds__(ALS_THREADS)
     scale_kernel(const float* __restrict__ Z, const double* __restrict__ lambda, int64_t I, int R,
                  FT* __restrict__ Y, const float* __restrict__ M, double* __restrict__ inner_part,
-                 const int* __restrict__ err) {
-  scale_body<FT>(Z, lambda, I, R, Y, M, inner_part, err, blockIdx.x, gridDim.x);
+                 const int* __restrict__ err, const uint32_t* __restrict__ mask) {
+  scale_body<FT>(Z, lambda, I, R, Y, M, inner_part, err, blockIdx.x, gridDim.x, mask);
 }
 
 __global__ void fit_kernel(const double* __restrict__ grams, int N, int R,
@@ -75,16 +75,17 @@ __global__ void copy_lambda_kernel(const double* __restrict__ src, int R, double
 }
 
 template <typename FT>
-spm_status launch_gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, cudaStream_t s) {
+spm_status launch_gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, cudaStream_t s,
+                       const uint32_t* mask) {
   const int R = p->R;
   spm_als_state& A = p->als;
   const int nb = als_row_blocks(I, A.gram_blocks);
   const int64_t rpb = ceil_div<int64_t>(I, nb);
   const FT* y = static_cast<const FT*>(Y);
   switch (gram_tile(R)) {
-    case 1: gram_partial_kernel<FT, 1><<<nb, ALS_THREADS, 0, s>>>(y, I, R, rpb, A.gram_part); break;
-    case 2: gram_partial_kernel<FT, 2><<<nb, ALS_THREADS, 0, s>>>(y, I, R, rpb, A.gram_part); break;
-    case 4: gram_partial_kernel<FT, 4><<<nb, ALS_THREADS, 0, s>>>(y, I, R, rpb, A.gram_part); break;
+    case 1: gram_partial_kernel<FT, 1><<<nb, ALS_THREADS, 0, s>>>(y, I, R, rpb, A.gram_part, mask); break;
+    case 2: gram_partial_kernel<FT, 2><<<nb, ALS_THREADS, 0, s>>>(y, I, R, rpb, A.gram_part, mask); break;
+    case 4: gram_partial_kernel<FT, 4><<<nb, ALS_THREADS, 0, s>>>(y, I, R, rpb, A.gram_part, mask); break;
     default: return SPM_ERR_UNSUPPORTED;
   }
   gram_reduce_kernel<<<std::max(1, std::min(1024, R * R / 8)), 256, 0, s>>>(
@@ -95,8 +96,10 @@ spm_status launch_gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, 
 
 }  // namespace
 
-spm_status gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, cudaStream_t s) {
-  return p->bf16 ? launch_gram<__nv_bfloat16>(p, Y, I, G, s) : launch_gram<float>(p, Y, I, G, s);
+spm_status gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, cudaStream_t s,
+                const uint32_t* mask) {
+  return p->bf16 ? launch_gram<__nv_bfloat16>(p, Y, I, G, s, mask)
+                 : launch_gram<float>(p, Y, I, G, s, mask);
 }
 
 spm_status ensure_als_state(spmttkrp_plan_s* p) {
@@ -143,22 +146,24 @@ spm_status als_sweep(spmttkrp_plan_s* p, void* const* factors, double* lambda, d
     SPM_TRY(run_mttkrp(p, d, factors, A.M, s));
     system_kernel<<<1, ALS_THREADS, 0, s>>>(A.gram, N, d, R, A.chol, A.winv, p->dev_err);
     const int nb = als_row_blocks(I, nb_solve);
-    if (R <= 32) solve_kernel<1><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err);
-    else solve_kernel<2><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err);
+    // rows without nonzeros in mode d have a zero update: passes skip them
+    const uint32_t* live = p->mode[d].empty_rows > 0 ? p->mode[d].rowmask : nullptr;
+    if (R <= 32) solve_kernel<1><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err, live);
+    else solve_kernel<2><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err, live);
     lambda_kernel<<<1, 256, 0, s>>>(A.colsq_part, nb, R, A.lambda_ws, p->dev_err);
     const bool last = d == N - 1;
     const int nbs = als_row_blocks(I, nb_solve);
     if (p->bf16)
       scale_kernel<__nv_bfloat16><<<nbs, ALS_THREADS, 0, s>>>(
           A.Z, A.lambda_ws, I, R, static_cast<__nv_bfloat16*>(factors[d]), last ? A.M : nullptr,
-          A.inner_part, p->dev_err);
+          A.inner_part, p->dev_err, live);
     else
       scale_kernel<float><<<nbs, ALS_THREADS, 0, s>>>(A.Z, A.lambda_ws, I, R,
                                                        static_cast<float*>(factors[d]),
                                                        last ? A.M : nullptr, A.inner_part,
-                                                       p->dev_err);
+                                                       p->dev_err, live);
     SPM_CUDA_TRY(cudaGetLastError());
-    SPM_TRY(gram(p, factors[d], I, A.gram + (size_t)d * R * R, s));
+    SPM_TRY(gram(p, factors[d], I, A.gram + (size_t)d * R * R, s, live));
     if (last) {
       fit_kernel<<<1, ALS_THREADS, 0, s>>>(A.gram, N, R, A.lambda_ws, A.inner_part, nbs,
                                            p->normX2, fit, lambda, p->dev_err);

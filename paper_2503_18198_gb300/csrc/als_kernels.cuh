@@ -58,6 +58,15 @@ __device__ __forceinline__ double warp_sum_strided(const double* __restrict__ x,
   return __shfl_sync(SPM_FULL_MASK, s, 0);
 }
 
+// Row i is non-empty (has a nonzero in the output mode) when its bit is set;
+// a null mask counts every row as non-empty.  Rows without nonzeros have a
+// zero MTTKRP row, so their update is exactly zero and their share of every
+// row pass below is exactly zero too: skipping them leaves each sum's bits
+// unchanged.
+__device__ __forceinline__ bool row_live(const uint32_t* __restrict__ mask, int64_t i) {
+  return !mask || ((__ldg(&mask[i >> 5]) >> (i & 31)) & 1u);
+}
+
 // Partial counts up to this are summed by one thread per entry (reads
 // coalesced across entries); more by one warp per entry.  The choice depends
 // on the count only, so a tensor's sums are the same in every launch shape.
@@ -97,10 +106,11 @@ __device__ __forceinline__ __nv_bfloat16 store_cvt<__nv_bfloat16>(float x) {
 template <typename FT, int GT>
 __device__ __forceinline__ void gram_partial_body(const FT* __restrict__ Y, int64_t I, int R,
                                                   int64_t rows_per_block, double* __restrict__ part,
-                                                  int vb) {
+                                                  int vb, const uint32_t* __restrict__ mask) {
   constexpr int RMAX = 16 * GT;
   constexpr int EPT = (RMAX * (RMAX + 1) / 2 + ALS_THREADS - 1) / ALS_THREADS;  // entries per thread
   __shared__ float tile[GRAM_TILE_ROWS][RMAX + 1];
+  __shared__ int live[GRAM_TILE_ROWS];
   const int64_t i0 = (int64_t)vb * rows_per_block;
   const int64_t i1 = std::min<int64_t>(I, i0 + rows_per_block);
   const int T = R * (R + 1) / 2;
@@ -118,12 +128,16 @@ __device__ __forceinline__ void gram_partial_body(const FT* __restrict__ Y, int6
   for (int64_t t0 = i0; t0 < i1; t0 += GRAM_TILE_ROWS) {
     const int nrow = (int)std::min<int64_t>(GRAM_TILE_ROWS, i1 - t0);
     __syncthreads();
+    if (threadIdx.x < GRAM_TILE_ROWS)
+      live[threadIdx.x] = threadIdx.x < nrow && row_live(mask, t0 + threadIdx.x);
+    __syncthreads();
     for (int e = threadIdx.x; e < GRAM_TILE_ROWS * RMAX; e += ALS_THREADS) {
       const int rr = e / RMAX, cc = e % RMAX;
-      tile[rr][cc] = (rr < nrow && cc < R) ? load_f<FT>(Y, (t0 + rr) * R + cc) : 0.f;
+      tile[rr][cc] = (live[rr] && cc < R) ? load_f<FT>(Y, (t0 + rr) * R + cc) : 0.f;
     }
     __syncthreads();
     for (int rr = 0; rr < nrow; ++rr) {
+      if (!live[rr]) continue;
 #pragma unroll
       for (int k = 0; k < EPT; ++k) df_add_prod(acc[k], tile[rr][er[k]], tile[rr][es[k]]);
     }
@@ -246,7 +260,8 @@ template <int RPL>
 __device__ __forceinline__ void solve_body(const float* __restrict__ M,
                                            const float* __restrict__ winv, int64_t I, int R,
                                            float* __restrict__ Z, double* __restrict__ colsq_part,
-                                           const int* __restrict__ err, int vb, int nvb) {
+                                           const int* __restrict__ err, int vb, int nvb,
+                                           const uint32_t* __restrict__ mask) {
   constexpr int ROWS = 4;
   __shared__ double red[ALS_THREADS / 32][32 * RPL];
   __shared__ float2 w_s[(32 * RPL) * (32 * RPL)];  // V^{-1} as (hi, lo) pairs
@@ -261,6 +276,12 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ M,
 #pragma unroll
   for (int j = 0; j < RPL; ++j) sq[j] = {0.f, 0.f};
   for (int64_t i0 = gwarp * ROWS; i0 < I; i0 += nwarps * ROWS) {
+    if (mask) {  // a group of empty rows: Z is not written (scale_body reads no Z there)
+      bool any = false;
+#pragma unroll
+      for (int q = 0; q < ROWS; ++q) any = any || (i0 + q < I && row_live(mask, i0 + q));
+      if (!any) continue;
+    }
     df acc[ROWS][RPL];
 #pragma unroll
     for (int q = 0; q < ROWS; ++q)
@@ -343,7 +364,8 @@ __device__ __forceinline__ void scale_body(const float* __restrict__ Z,
                                            const double* __restrict__ lambda, int64_t I, int R,
                                            FT* __restrict__ Y, const float* __restrict__ M,
                                            double* __restrict__ inner_part,
-                                           const int* __restrict__ err, int vb, int nvb) {
+                                           const int* __restrict__ err, int vb, int nvb,
+                                           const uint32_t* __restrict__ mask) {
   __shared__ double red[ALS_THREADS];
   if (*err) return;
   // each thread walks a fixed rank r = t % R over rows (t / R) + k * stride
@@ -358,11 +380,12 @@ __device__ __forceinline__ void scale_body(const float* __restrict__ Z,
   if (active) {
     const int64_t stride = (int64_t)nvb * per;
     for (int64_t i = (int64_t)vb * per + sub; i < I; i += stride) {
-      const float z = Z[i * R + r];
+      const bool lv = row_live(mask, i);
+      const float z = lv ? Z[i * R + r] : 0.f;
       const float y = lam > 0.0 ? z * inv : z;
       const FT ys = store_cvt<FT>(y);
       Y[i * R + r] = ys;
-      if (M) df_add_prod(in, M[i * R + r], load_f<FT>(&ys, 0));
+      if (M && lv) df_add_prod(in, M[i * R + r], load_f<FT>(&ys, 0));
     }
   }
   if (!M) return;

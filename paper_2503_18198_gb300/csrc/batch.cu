@@ -55,9 +55,11 @@ __global__ void __launch_bounds__(ALS_THREADS)
   const BatchTensor& b = bt[tv.x];
   if (!b.active) return;
   if (b.R <= 32)
-    solve_body<1>(b.M, b.winv, b.dims[mode], b.R, b.Z, b.colsq_part, b.err, tv.y, b.nb_solve[mode]);
+    solve_body<1>(b.M, b.winv, b.dims[mode], b.R, b.Z, b.colsq_part, b.err, tv.y, b.nb_solve[mode],
+                  b.live[mode]);
   else
-    solve_body<2>(b.M, b.winv, b.dims[mode], b.R, b.Z, b.colsq_part, b.err, tv.y, b.nb_solve[mode]);
+    solve_body<2>(b.M, b.winv, b.dims[mode], b.R, b.Z, b.colsq_part, b.err, tv.y, b.nb_solve[mode],
+                  b.live[mode]);
 }
 
 __global__ void batch_lambda_kernel(const BatchTensor* __restrict__ bt, const int2* __restrict__ it,
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(ALS_THREADS)
   if (!b.active) return;
   const bool last = mode == b.N - 1;
   scale_body<FT>(b.Z, b.lambda_ws, b.dims[mode], b.R, static_cast<FT*>(b.fac[mode]),
-                 last ? b.M : nullptr, b.inner_part, b.err, tv.y, b.nb_scale[mode]);
+                 last ? b.M : nullptr, b.inner_part, b.err, tv.y, b.nb_scale[mode], b.live[mode]);
 }
 
 // Gram partials of factor `mode` (also used for the initial Grams).
@@ -89,9 +91,9 @@ __global__ void __launch_bounds__(ALS_THREADS)
   const int64_t I = b.dims[mode];
   const int64_t rpb = b.gram_rpb[mode];
   switch (gram_tile(b.R)) {
-    case 1: gram_partial_body<FT, 1>(y, I, b.R, rpb, b.gram_part, tv.y); break;
-    case 2: gram_partial_body<FT, 2>(y, I, b.R, rpb, b.gram_part, tv.y); break;
-    default: gram_partial_body<FT, 4>(y, I, b.R, rpb, b.gram_part, tv.y); break;
+    case 1: gram_partial_body<FT, 1>(y, I, b.R, rpb, b.gram_part, tv.y, b.live[mode]); break;
+    case 2: gram_partial_body<FT, 2>(y, I, b.R, rpb, b.gram_part, tv.y, b.live[mode]); break;
+    default: gram_partial_body<FT, 4>(y, I, b.R, rpb, b.gram_part, tv.y, b.live[mode]); break;
   }
 }
 
@@ -190,6 +192,7 @@ spm_status batch_add(spm_batch_s* B, spmttkrp_plan_s* p, void* const* factors, d
     const int64_t I = p->dims[d];
     b.dims[d] = I;
     b.rowmask[d] = p->mode[d].rowmask;
+    b.live[d] = p->mode[d].empty_rows > 0 ? p->mode[d].rowmask : nullptr;
     MttkrpArgs& a = b.margs[d];
     a = MttkrpArgs{};
     a.rec = p->mode[d].rec;

@@ -25,6 +25,7 @@ struct BatchTensor {
   void* fac[SPM_MAX_MODES];
   int64_t dims[SPM_MAX_MODES];
   uint32_t* rowmask[SPM_MAX_MODES];
+  const uint32_t* live[SPM_MAX_MODES];  // rowmask when the mode has empty rows, else null
   int nb_gram[SPM_MAX_MODES];   // virtual blocks of the row passes per mode
   int nb_solve[SPM_MAX_MODES];
   int nb_scale[SPM_MAX_MODES];

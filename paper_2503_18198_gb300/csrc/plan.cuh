@@ -96,7 +96,9 @@ spm_status als_sweep(spmttkrp_plan_s* p, void* const* factors, double* lambda,
                      double* fit, cudaStream_t s);
 
 // G = Y^T Y (FP64, R x R) of a stored factor with the plan's block split (als.cu).
-spm_status gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, cudaStream_t s);
+// With `mask`, rows whose bit is clear are known to be zero and are skipped.
+spm_status gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, cudaStream_t s,
+                const uint32_t* mask = nullptr);
 
 // Allocate the plan's CP-ALS workspace on first use (als.cu).
 spm_status ensure_als_state(spmttkrp_plan_s* p);
