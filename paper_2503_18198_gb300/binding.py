@@ -580,3 +580,45 @@ def spm_selftest_wait_timeout(limit: int = 4096, stream=None) -> int:
 def spm_inject_alloc_failure(k: int):
     """Make the k-th plan allocation from now fail with SPM_ERR_OOM (k < 0: off)."""
     load().spm_inject_alloc_failure(int(k))
+
+
+# Same-named functions for the serving entry points (the Server methods do the
+# marshalling).
+def spm_server_create(budget_bytes: int, max_active: int = 64, flags: int = 0,
+                      nnz_per_partition: int = 1 << 17) -> Server:
+    return Server(budget_bytes, max_active, flags, nnz_per_partition)
+
+
+def spm_server_submit(server: Server, dims, idx, vals, rank: int, init, tol: float = 1e-4,
+                      max_sweeps: int = 50) -> int:
+    return server.submit(dims, idx, vals, rank, init, tol, max_sweeps)
+
+
+def spm_server_resume(server: Server, dims, idx, vals, rank: int, init, sweeps_done: int,
+                      prev_fit: float, tol: float = 1e-4, max_sweeps: int = 50) -> int:
+    return server.submit(dims, idx, vals, rank, init, tol, max_sweeps,
+                         resume=(sweeps_done, prev_fit))
+
+
+def spm_server_step(server: Server):
+    return server.step()
+
+
+def spm_server_job(server: Server, job: int) -> JobInfo:
+    return server.info(job)
+
+
+def spm_server_result(server: Server, job: int, stream=None):
+    return server.result(job, stream)
+
+
+def spm_server_snapshot(server: Server, job: int, stream=None):
+    return server.snapshot(job, stream)
+
+
+def spm_server_usage(server: Server):
+    return server.usage()
+
+
+def spm_server_destroy(server: Server):
+    server.destroy()

@@ -35,6 +35,9 @@ def test_library_builds_and_exports_every_declared_symbol():
     for n in sorted(names):
         assert hasattr(lib, n), f"{n} declared in include/ but not exported"
     assert set(binding.SYMBOLS) <= names
+    # the Python binding has a function of the same name for every entry point
+    for n in sorted(names):
+        assert callable(getattr(binding, n, None)), f"{n} has no binding function"
 
 
 def test_status_strings_and_no_device_behaviour():
