@@ -18,17 +18,17 @@ spm_status launch_batch_mttkrp_bf16(int kc, const BatchTensor* bt, const int2* i
 
 namespace {
 
-constexpr int64_t BATCH_ZERO_CHUNK = 1 << 16;  // output elements per zero-fill item
+constexpr int64_t BATCH_ZERO_WORDS = 1 << 10;  // row-bitmap words per zero-fill item
 
 __global__ void batch_zero_kernel(const BatchTensor* __restrict__ bt, const int2* __restrict__ it,
                                   int mode) {
   const int2 tc = it[blockIdx.x];
   const BatchTensor& b = bt[tc.x];
   if (!b.active) return;
-  const int64_t n = b.dims[mode] * b.R;
-  const int64_t x0 = (int64_t)tc.y * BATCH_ZERO_CHUNK;
-  const int64_t x1 = std::min<int64_t>(n, x0 + BATCH_ZERO_CHUNK);
-  zero_empty_rows_body(b.rowmask[mode], b.R, b.M, x0 + threadIdx.x, x1, blockDim.x);
+  const int64_t words = (b.dims[mode] + 31) / 32;
+  const int64_t w0 = (int64_t)tc.y * BATCH_ZERO_WORDS;
+  const int64_t w1 = std::min<int64_t>(words, w0 + BATCH_ZERO_WORDS);
+  zero_empty_rows_body(b.rowmask[mode], b.dims[mode], b.R, b.M, w0 + threadIdx.x, w1, blockDim.x);
 }
 
 __global__ void batch_fixup_kernel(const BatchTensor* __restrict__ bt, const int2* __restrict__ it,
@@ -274,7 +274,7 @@ spm_status batch_commit(spm_batch_s* B, cudaStream_t s) {
       // an empty tensor has no partition items: its row masks are all
       // clear, so the zero-fill items cover its whole output
       if (d < p->N && (p->nnz == 0 || p->mode[d].empty_rows > 0)) {
-        const int64_t chunks = ceil_div<int64_t>(p->dims[d] * p->R, BATCH_ZERO_CHUNK);
+        const int64_t chunks = ceil_div<int64_t>((p->dims[d] + 31) / 32, BATCH_ZERO_WORDS);
         for (int64_t c = 0; c < chunks; ++c) v.push_back(make_int2(t, (int)c));
       }
     }

@@ -28,8 +28,8 @@ namespace {
 // Rows without nonzeros (bit clear in `mask`) are written as zeros.
 __global__ void zero_empty_rows_kernel(const uint32_t* __restrict__ mask, int64_t I, int R,
                                        float* __restrict__ out) {
-  zero_empty_rows_body(mask, R, out, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, I * R,
-                       (int64_t)gridDim.x * blockDim.x);
+  zero_empty_rows_body(mask, I, R, out, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                       (I + 31) / 32, (int64_t)gridDim.x * blockDim.x);
 }
 
 // One warp per partition z (see mttkrp_fixup_body).
@@ -89,8 +89,8 @@ spm_status run_mttkrp(spmttkrp_plan_s* p, int mode, const void* const* factors, 
   if (c.scheme == 1) {
     SPM_CUDA_TRY(cudaMemsetAsync(out, 0, out_bytes, s));
   } else if (c.empty_rows > 0) {
-    const int64_t n4 = (int64_t)a.I * R;
-    const int blocks = (int)std::min<int64_t>(ceil_div<int64_t>(n4, 256), 152 * 16);
+    const int64_t words = (a.I + 31) / 32;
+    const int blocks = (int)std::min<int64_t>(ceil_div<int64_t>(words, 256), 152 * 8);
     zero_empty_rows_kernel<<<blocks, 256, 0, s>>>(c.rowmask, a.I, R, out);
     SPM_CUDA_TRY(cudaGetLastError());
   }

@@ -785,14 +785,27 @@ __device__ __forceinline__ void mttkrp_fixup_body(const float* __restrict__ cta_
   }
 }
 
-// Rows [x0, x1) of an I x R output whose bit in `mask` is clear are zeroed
-// (x counts elements, not rows).
-__device__ __forceinline__ void zero_empty_rows_body(const uint32_t* __restrict__ mask, int R,
-                                                     float* __restrict__ out, int64_t x0,
-                                                     int64_t x1, int64_t xstep) {
-  for (int64_t x = x0; x < x1; x += xstep) {
-    const int64_t row = x / R;
-    if (!((__ldg(&mask[row >> 5]) >> (row & 31)) & 1u)) out[x] = 0.f;
+// Rows of an I x R output whose bit in `mask` is clear are zeroed, for the
+// bitmap words [w0, w1) (word w covers rows 32w .. 32w+31), one word per
+// thread stepping by wstep.  Full words cost one load; an empty row is
+// cleared with 16-byte stores when R allows.
+__device__ __forceinline__ void zero_empty_rows_body(const uint32_t* __restrict__ mask, int64_t I,
+                                                     int R, float* __restrict__ out, int64_t w0,
+                                                     int64_t w1, int64_t wstep) {
+  for (int64_t w = w0; w < w1; w += wstep) {
+    uint32_t clear = ~__ldg(&mask[w]);
+    while (clear) {
+      const int b = __ffs(clear) - 1;
+      clear &= clear - 1;
+      const int64_t row = w * 32 + b;
+      if (row >= I) break;
+      float* dst = out + row * R;
+      if ((R & 3) == 0) {
+        for (int c = 0; c < R; c += 4) *reinterpret_cast<float4*>(dst + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        for (int c = 0; c < R; ++c) dst[c] = 0.f;
+      }
+    }
   }
 }
 
