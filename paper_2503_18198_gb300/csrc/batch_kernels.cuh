@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(MT_THREADS, 1)
     mttkrp_batch_kernel(const BatchTensor* __restrict__ bt, const int2* __restrict__ items,
                         int nitems, int* __restrict__ queue, int mode) {
   using C = BatchClass<KC>;
-  constexpr int V = 16 / (int)sizeof(FT);
+  // the lane layout the single-tensor kernel picks for this (type, rank)
+  constexpr int V = (sizeof(FT) == 2 && C::R <= 32) ? 4 : 16 / (int)sizeof(FT);
   __shared__ int item;
   for (;;) {
     if (threadIdx.x == 0) item = atomicAdd(queue, 1);

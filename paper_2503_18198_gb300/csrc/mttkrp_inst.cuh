@@ -15,6 +15,17 @@ template <typename FT, int NIN, bool LEAN = false>
 MttkrpKernelFn pick_mttkrp_t(int R) {
   constexpr int RI = record_int4s(NIN > 0 ? NIN + 1 : SPM_MAX_MODES);
   constexpr int VEC = 16 / (int)sizeof(FT);
+  if constexpr (sizeof(FT) == 2) {  // BF16 with R <= 32: 8-byte lane loads
+    if (R % 4 == 0 && R <= 32) {
+      switch (R / 4) {
+        case 1: return &mttkrp_kernel<RI, NIN, FT, 4, 1, 1, LEAN>;
+        case 2: return &mttkrp_kernel<RI, NIN, FT, 4, 2, 1, LEAN>;
+        case 4: return &mttkrp_kernel<RI, NIN, FT, 4, 4, 1, LEAN>;
+        case 8: return &mttkrp_kernel<RI, NIN, FT, 4, 8, 1, LEAN>;
+        default: break;
+      }
+    }
+  }
   if (R % VEC == 0) {
     switch (R / VEC) {
       case 1: return &mttkrp_kernel<RI, NIN, FT, VEC, 1, 1, LEAN>;

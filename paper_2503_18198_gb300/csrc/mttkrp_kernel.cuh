@@ -34,6 +34,8 @@
 //    bitmap of non-empty rows.
 #pragma once
 
+#include <type_traits>
+
 #include "plan.cuh"
 
 namespace spm {
@@ -146,6 +148,26 @@ struct Slice<__nv_bfloat16, 8> {
   }
 };
 
+// BF16 rows of R <= 32: 8-byte loads (4 values per lane), so that a warp step
+// holds as many nonzeros as the FP32 layout of the same rank.
+template <>
+struct Slice<__nv_bfloat16, 4> {
+  static constexpr int RAWN = 2;
+  static __device__ __forceinline__ void load(const void* base, int64_t row, int R, int r0,
+                                              uint32_t* raw) {
+    const uint2 x = __ldg(reinterpret_cast<const uint2*>(
+        static_cast<const __nv_bfloat16*>(base) + row * R + r0));
+    raw[0] = x.x; raw[1] = x.y;
+  }
+  static __device__ __forceinline__ void cvt(const uint32_t* raw, float* f) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      f[2 * i] = __uint_as_float(raw[i] << 16);
+      f[2 * i + 1] = __uint_as_float(raw[i] & 0xFFFF0000u);
+    }
+  }
+};
+
 template <>
 struct Slice<float, 1> {
   static constexpr int RAWN = 1;
@@ -221,7 +243,11 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
 #ifdef SPM_MT_BATCH
   constexpr int U = NIN == 0 ? 1 : SPM_MT_BATCH;
 #else
-  constexpr int U = NIN == 0 ? 1 : (PIPE_REGS <= 4 ? 4 : (PIPE_REGS <= 8 ? 2 : 1));
+  // 8-byte lanes (BF16, R <= 32) convert to as many floats as 16-byte FP32
+  // lanes: the same two-step batch keeps them within 64 registers
+  constexpr int U = NIN == 0 ? 1
+                  : (VEC * (int)sizeof(FT) == 8 ? 2
+                     : (PIPE_REGS <= 4 ? 4 : (PIPE_REGS <= 8 ? 2 : 1)));
 #endif
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int next_unit;
@@ -252,13 +278,15 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
   // Vector path with the rank fixed at compile time (R == VEC * LPN * CPL):
   // full steps are processed without per-step predication, gathers address
   // rows with a constant stride from per-lane base pointers.
-  constexpr bool FAST = NIN > 0 && VEC * (int)sizeof(FT) == 16;
+  constexpr int LANE_BYTES = VEC * (int)sizeof(FT);
+  constexpr bool FAST = NIN > 0 && (LANE_BYTES == 16 || LANE_BYTES == 8);
+  using LdT = typename std::conditional<LANE_BYTES == 16, uint4, uint2>::type;
   constexpr int RT = VEC * LPN * CPL;
   constexpr int NINF = NIN > 0 ? NIN : 1;
-  const uint4* facb[NINF];
+  const LdT* facb[NINF];
 #pragma unroll
   for (int m = 0; m < NINF; ++m)
-    facb[m] = reinterpret_cast<const uint4*>(static_cast<const FT*>(a.fac[m]) + sub * VEC);
+    facb[m] = reinterpret_cast<const LdT*>(static_cast<const FT*>(a.fac[m]) + sub * VEC);
 
   if (lane == 0) {
 #pragma unroll
@@ -468,14 +496,21 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
 #if SPM_MT_REUSE
                   if (m == 0 && !fresh0[uu]) continue;  // taken from the previous step below
 #endif
-                  const uint4* src = facb[m] + (size_t)(uint32_t)w[uu][1 + m] * (RT * sizeof(FT) / 16) + c * LPN;
+                  const LdT* src = facb[m] +
+                                   (size_t)(uint32_t)w[uu][1 + m] * (RT * sizeof(FT) / sizeof(LdT)) +
+                                   c * LPN;
+                  if constexpr (LANE_BYTES == 16) {
 #if SPM_L2_HINTS
-                  const uint4 x = ld_nc_v4_pol(src, pol_rows);
+                    const uint4 x = ld_nc_v4_pol(src, pol_rows);
 #else
-                  const uint4 x = __ldg(src);
+                    const uint4 x = __ldg(src);
 #endif
-                  y[uu][m][c][0] = x.x; y[uu][m][c][1] = x.y;
-                  y[uu][m][c][2] = x.z; y[uu][m][c][3] = x.w;
+                    y[uu][m][c][0] = x.x; y[uu][m][c][1] = x.y;
+                    y[uu][m][c][2] = x.z; y[uu][m][c][3] = x.w;
+                  } else {
+                    const uint2 x = __ldg(src);
+                    y[uu][m][c][0] = x.x; y[uu][m][c][1] = x.y;
+                  }
                 }
 #if SPM_MT_REUSE
 #pragma unroll
