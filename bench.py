@@ -206,8 +206,23 @@ def cpu_baseline(dims, idx, vals, Y, R, target_s):
                       f"{dt:.1f} s single-threaded FP64"}
 
 
+def arm_config(nnz, dims, R, world):
+    """The `config` object of the headline line (both arms)."""
+    return {"workload": WORKLOAD, "nnz": nnz, "dims": list(dims), "rank": R,
+            "factor_dtype": "fp32", "policy": "balanced",
+            "step": "spMTTKRP along modes 0,1,2 on resident mode copies",
+            "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+
+
+REFERENCE_SECONDS = 120.0  # wall-time target of a whole reference run
+
+
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 oracle on the host cores, same metric/unit."""
+    """Reference arm: the FP64 oracle on the host cores, same metric/unit.
+    Each step runs the oracle's MTTKRP along all modes on the workload's first
+    n nonzeros, n sized from a probe so that warm-up plus the timed steps take
+    about REFERENCE_SECONDS."""
     if rank != 0:
         return
     import synth
@@ -215,7 +230,10 @@ def run_reference(args, rank, world):
     torch.set_num_threads(max(1, os.cpu_count() or 1))
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     dims, idx, vals, R, Y = synth.preset_torch("scale", nnz=args.nnz, device=dev)
-    n = min(args.nnz, 2_000_000)
+    probe = min(args.nnz, 200_000)
+    dt, _ = time_oracle(dims, *host_sample(dims, idx, vals, Y, probe), R)
+    per_step = REFERENCE_SECONDS / max(1, args.steps + args.warmup)
+    n = int(min(args.nnz, 2_000_000, max(20_000, probe * per_step / max(dt, 1e-6))))
     h = host_sample(dims, idx, vals, Y, n)
     for _ in range(args.warmup):
         time_oracle(dims, *h, R)
@@ -226,11 +244,13 @@ def run_reference(args, rank, world):
         tot_b += b
     v = tot_b / tot_s / 1e9
     sample = f"first {n} of the workload's nonzeros per step, all 3 modes, single-threaded FP64 oracle"
+    cfg = arm_config(int(vals.numel()), dims, R, world)
+    cfg["sample_nnz"] = n
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_nnz": n},
+        "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
         flush=True)
@@ -374,11 +394,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nnz": nnz, "dims": list(dims), "rank": R,
-                       "factor_dtype": "fp32", "policy": "balanced",
-                       "step": "spMTTKRP along modes 0,1,2 on resident mode copies",
-                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "config": arm_config(nnz, dims, R, world),
             "per_mode_ms": [round(m, 4) for m in mode_ms],
             "per_mode_roofline_frac": [round(b / (m * 1e-3) / 1e9 / peak, 4)
                                        for b, m in zip(B, mode_ms)],
