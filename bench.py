@@ -192,6 +192,22 @@ def time_oracle(dims, h_idx, h_vals, h_Y, R):
     return dt, sum(algorithmic_bytes(dims, n, R, distinct))
 
 
+def host_info():
+    """Core count and CPU model of the host the oracle runs on."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
 def cpu_baseline(dims, idx, vals, Y, R, target_s):
     """The oracle as it stands, single-threaded, on a prefix sample of the
     workload's nonzeros (the same tensor's first nonzeros in draw order)."""
@@ -203,7 +219,8 @@ def cpu_baseline(dims, idx, vals, Y, R, target_s):
     dt, b = time_oracle(dims, *h, R)
     return {"value": b / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {n} of the workload's nonzeros (draw order), all 3 modes, "
-                      f"{dt:.1f} s single-threaded FP64"}
+                      f"{dt:.1f} s single-threaded FP64",
+            "host": host_info()}
 
 
 def arm_config(nnz, dims, R, world):
@@ -251,7 +268,8 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": cfg,
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_info()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
         flush=True)
 
