@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(MT_THREADS, 1)
                         int nitems, int* __restrict__ queue, int mode) {
   using C = BatchClass<KC>;
   // the lane layout the single-tensor kernel picks for this (type, rank)
-  constexpr int V = (sizeof(FT) == 2 && C::R <= 32) ? 4 : 16 / (int)sizeof(FT);
+  constexpr int V = (sizeof(FT) == 2 && C::N == 3 && C::R <= 32) ? 4 : 16 / (int)sizeof(FT);
   __shared__ int item;
   for (;;) {
     if (threadIdx.x == 0) item = atomicAdd(queue, 1);

@@ -15,7 +15,7 @@ template <typename FT, int NIN, bool LEAN = false>
 MttkrpKernelFn pick_mttkrp_t(int R) {
   constexpr int RI = record_int4s(NIN > 0 ? NIN + 1 : SPM_MAX_MODES);
   constexpr int VEC = 16 / (int)sizeof(FT);
-  if constexpr (sizeof(FT) == 2) {  // BF16 with R <= 32: 8-byte lane loads
+  if constexpr (sizeof(FT) == 2 && NIN == 2) {  // 3-mode BF16 with R <= 32: 8-byte lane loads
     if (R % 4 == 0 && R <= 32) {
       switch (R / 4) {
         case 1: return &mttkrp_kernel<RI, NIN, FT, 4, 1, 1, LEAN>;

@@ -87,6 +87,12 @@ enum : int {
 #ifndef SPM_MT_F32X2
 #define SPM_MT_F32X2 1  // 1: packed FP32-pair arithmetic in the full-step path
 #endif
+#ifndef SPM_MT_PAIRS
+#define SPM_MT_PAIRS 1  // 1: FP32 rows and accumulators kept as FP32 pairs through the full-step path
+#endif
+#ifndef SPM_MT_PAIRS_BF16
+#define SPM_MT_PAIRS_BF16 1  // 1: the same for BF16 factors (raw words widened to FP32 pairs)
+#endif
 #ifndef SPM_MT_REUSE
 #define SPM_MT_REUSE 0  // 1: a slot keeps its first input mode's row and skips a repeated gather
 #endif
@@ -148,8 +154,9 @@ struct Slice<__nv_bfloat16, 8> {
   }
 };
 
-// BF16 rows of R <= 32: 8-byte loads (4 values per lane), so that a warp step
-// holds as many nonzeros as the FP32 layout of the same rank.
+// BF16 rows of R <= 32 in 3-mode tensors: 8-byte loads (4 values per lane),
+// so that a warp step holds as many nonzeros as the FP32 layout of the same
+// rank (measured faster for 3 modes, slower for 5).
 template <>
 struct Slice<__nv_bfloat16, 4> {
   static constexpr int RAWN = 2;
@@ -281,6 +288,12 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
   constexpr int LANE_BYTES = VEC * (int)sizeof(FT);
   constexpr bool FAST = NIN > 0 && (LANE_BYTES == 16 || LANE_BYTES == 8);
   using LdT = typename std::conditional<LANE_BYTES == 16, uint4, uint2>::type;
+  // FP32 factors: a lane's 16-byte slice is loaded as two FP32 pairs and the
+  // running sums are kept as pairs, so the packed arithmetic needs no moves.
+  // BF16 factors: each raw word (two BF16 ranks) widens to one FP32 pair.
+  constexpr bool P32 = std::is_same<FT, float>::value;
+  constexpr bool PAIRS = FAST && ((P32 && SPM_MT_PAIRS && LANE_BYTES == 16) ||
+                                  (!P32 && SPM_MT_PAIRS_BF16));
   constexpr int RT = VEC * LPN * CPL;
   constexpr int NINF = NIN > 0 ? NIN : 1;
   const LdT* facb[NINF];
@@ -457,7 +470,109 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
         const int nst = (n + G - 1) / G;
         const bool pure = tile_row(0) == cur && tile_row(n - 1) == cur;
         int j_fast = 0;
-        if constexpr (FAST) {
+        if constexpr (PAIRS) {
+          // Full steps, U at a time.  Unless the tile lies on the current
+          // row, each batch of U steps takes one vote, and a batch that
+          // leaves the row passes its steps to step_rows.  Same roundings as
+          // the scalar path: (val * y_a) * y_b ... then one fused multiply-add
+          // into the running sum on the row, a product then an add in
+          // step_rows.
+          constexpr int H = VEC / 2;
+          const int nb = ((n / G) / U) * U;
+          uint64_t ap[CPL][H];
+#pragma unroll
+          for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int e = 0; e < H; ++e) ap[c][e] = f2_pack(acc[c][2 * e], acc[c][2 * e + 1]);
+          // FP32: the loaded pairs; BF16: raw words, widened when used
+          using YT = typename std::conditional<P32, uint64_t, uint32_t>::type;
+          auto pair = [](YT x) -> uint64_t {
+            if constexpr (P32) return x;
+            else return f2_pack(__uint_as_float((uint32_t)x << 16), __uint_as_float((uint32_t)x & 0xFFFF0000u));
+          };
+          for (int j = 0; j < nb; j += U) {
+            int w[U][W];
+            YT y[U][NINF][CPL][H];
+#pragma unroll
+            for (int uu = 0; uu < U; ++uu) load_rec((j + uu) * G + slot, w[uu]);
+#pragma unroll
+            for (int uu = 0; uu < U; ++uu)
+#pragma unroll
+              for (int m = 0; m < NINF; ++m)
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                  const LdT* src =
+                      facb[m] + (size_t)(uint32_t)w[uu][1 + m] * (RT * sizeof(FT) / sizeof(LdT)) + c * LPN;
+                  if constexpr (P32) {
+                    const ulonglong2 x = ld_nc_v2_u64(src);
+                    y[uu][m][c][0] = x.x;
+                    y[uu][m][c][1] = x.y;
+                  } else if constexpr (LANE_BYTES == 16) {
+                    const uint4 x = __ldg(src);
+                    y[uu][m][c][0] = x.x; y[uu][m][c][1] = x.y;
+                    y[uu][m][c][2] = x.z; y[uu][m][c][3] = x.w;
+                  } else {
+                    const uint2 x = __ldg(src);
+                    y[uu][m][c][0] = x.x; y[uu][m][c][1] = x.y;
+                  }
+                }
+            bool same = pure;
+            if (!pure) {
+              bool ok = true;
+#pragma unroll
+              for (int uu = 0; uu < U; ++uu) ok = ok && w[uu][0] == cur;
+              same = __all_sync(SPM_FULL_MASK, ok);
+            }
+            if (same) {
+#pragma unroll
+              for (int uu = 0; uu < U; ++uu) {
+                const float val = __int_as_float(w[uu][NINF + 1]);
+                const uint64_t vv = f2_pack(val, val);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                  for (int e = 0; e < H; ++e) {
+                    uint64_t g = f2_mul(vv, pair(y[uu][0][c][e]));
+#pragma unroll
+                    for (int m = 1; m + 1 < NINF; ++m) g = f2_mul(g, pair(y[uu][m][c][e]));
+                    ap[c][e] = NINF > 1 ? f2_fma(g, pair(y[uu][NINF - 1][c][e]), ap[c][e])
+                                        : f2_add(ap[c][e], g);
+                  }
+              }
+            } else {
+#pragma unroll
+              for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int e = 0; e < H; ++e) f2_unpack(ap[c][e], acc[c][2 * e], acc[c][2 * e + 1]);
+#pragma unroll
+              for (int uu = 0; uu < U; ++uu) {
+                const float val = __int_as_float(w[uu][NINF + 1]);
+                const uint64_t vv = f2_pack(val, val);
+                float v[CPL][VEC];
+#pragma unroll
+                for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                  for (int e = 0; e < H; ++e) {
+                    uint64_t g = f2_mul(vv, pair(y[uu][0][c][e]));
+#pragma unroll
+                    for (int m = 1; m + 1 < NINF; ++m) g = f2_mul(g, pair(y[uu][m][c][e]));
+                    if (NINF > 1) g = f2_mul(g, pair(y[uu][NINF - 1][c][e]));
+                    f2_unpack(g, v[c][2 * e], v[c][2 * e + 1]);
+                  }
+                step_rows(w[uu][0], v);
+              }
+#pragma unroll
+              for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int e = 0; e < H; ++e) ap[c][e] = f2_pack(acc[c][2 * e], acc[c][2 * e + 1]);
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int e = 0; e < H; ++e) f2_unpack(ap[c][e], acc[c][2 * e], acc[c][2 * e + 1]);
+          j_fast = nb;
+        } else if constexpr (FAST) {
           // full steps (a record in every slot), U at a time
           const int nb = ((n / G) / U) * U;
 #if SPM_MT_REUSE
