@@ -40,12 +40,12 @@ __global__ void __launch_bounds__(ALS_THREADS)
   system_body(grams, N, d, R, V, winv, err);
 }
 
-template <int RPL>
+template <int RPL, int LPR>
 __global__ void __launch_bounds__(ALS_THREADS)
     solve_kernel(const float* __restrict__ M, const float* __restrict__ winv, int64_t I, int R,
                  float* __restrict__ Z, double* __restrict__ colsq_part,
                  const int* __restrict__ err, const uint32_t* __restrict__ mask) {
-  solve_body<RPL>(M, winv, I, R, Z, colsq_part, err, blockIdx.x, gridDim.x, mask);
+  solve_body<RPL, LPR>(M, winv, I, R, Z, colsq_part, err, blockIdx.x, gridDim.x, mask);
 }
 
 __global__ void lambda_kernel(const double* __restrict__ colsq_part, int nblocks, int R,
@@ -148,8 +148,14 @@ spm_status als_sweep(spmttkrp_plan_s* p, void* const* factors, double* lambda, d
     const int nb = als_row_blocks(I, nb_solve);
     // rows without nonzeros in mode d have a zero update: passes skip them
     const uint32_t* live = p->mode[d].empty_rows > 0 ? p->mode[d].rowmask : nullptr;
-    if (R <= 32) solve_kernel<1><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err, live);
-    else solve_kernel<2><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err, live);
+    if (R <= 8)
+      solve_kernel<1, 8><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err, live);
+    else if (R <= 16)
+      solve_kernel<1, 16><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err, live);
+    else if (R <= 32)
+      solve_kernel<1, 32><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err, live);
+    else
+      solve_kernel<2, 32><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err, live);
     lambda_kernel<<<1, 256, 0, s>>>(A.colsq_part, nb, R, A.lambda_ws, p->dev_err);
     const bool last = d == N - 1;
     const int nbs = als_row_blocks(I, nb_solve);

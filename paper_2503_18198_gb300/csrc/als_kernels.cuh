@@ -156,22 +156,52 @@ __device__ __forceinline__ void gram_partial_body(const FT* __restrict__ Y, int6
 
 // G = sum over blocks of the partials (FP64, fixed order): one warp per
 // entry; virtual block vb of nvb takes every (nvb * warps)-th entry.
+// Each entry's sum has the same order in both forms as one thread (or one
+// warp, then warp_sum_strided's tree) summing it alone; GR_ENTRIES entries
+// are summed side by side so that their loads are in flight together.
+constexpr int GR_ENTRIES = 4;
 __device__ __forceinline__ void gram_reduce_body(const double* __restrict__ part, int nblocks,
                                                  int R, double* __restrict__ G,
                                                  const int* __restrict__ err, int vb, int nvb) {
   if (warp_err(err)) return;
+  const int RR = R * R;
   if (nblocks <= ALS_SERIAL_PARTIALS) {
-    for (int e = vb * blockDim.x + threadIdx.x; e < R * R; e += nvb * blockDim.x) {
-      double v = 0.0;
-      for (int b = 0; b < nblocks; ++b) v += part[(int64_t)b * R * R + e];
-      G[e] = v;
+    // thread t takes entries e, e + step, ..., GR_ENTRIES of them at a time
+    const int step = nvb * blockDim.x;
+    for (int e = vb * blockDim.x + threadIdx.x; e < RR; e += GR_ENTRIES * step) {
+      double v[GR_ENTRIES];
+#pragma unroll
+      for (int k = 0; k < GR_ENTRIES; ++k) v[k] = 0.0;
+#pragma unroll 4
+      for (int b = 0; b < nblocks; ++b) {
+        const double* pb = part + (int64_t)b * RR + e;
+#pragma unroll
+        for (int k = 0; k < GR_ENTRIES; ++k)
+          if (e + k * step < RR) v[k] += pb[k * step];
+      }
+#pragma unroll
+      for (int k = 0; k < GR_ENTRIES; ++k)
+        if (e + k * step < RR) G[e + k * step] = v[k];
     }
     return;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int e = vb * nw + warp; e < R * R; e += nvb * nw) {
-    const double v = warp_sum_strided(part + e, nblocks, (int64_t)R * R, lane);
-    if (lane == 0) G[e] = v;
+  for (int e = (vb * nw + warp) * GR_ENTRIES; e < RR; e += nvb * nw * GR_ENTRIES) {
+    double v[GR_ENTRIES];
+#pragma unroll
+    for (int k = 0; k < GR_ENTRIES; ++k) v[k] = 0.0;
+    for (int b = lane; b < nblocks; b += 32) {
+      const double* pb = part + (int64_t)b * RR + e;
+#pragma unroll
+      for (int k = 0; k < GR_ENTRIES; ++k)
+        if (e + k < RR) v[k] += pb[k];
+    }
+#pragma unroll
+    for (int k = 0; k < GR_ENTRIES; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(SPM_FULL_MASK, v[k], o);
+      if (lane == 0 && e + k < RR) G[e + k] = v[k];
+    }
   }
 }
 
@@ -253,20 +283,27 @@ __device__ __forceinline__ void system_body(const double* __restrict__ grams, in
 }
 
 // ---------------------------------------------------------------------------
-// Z = M W (double-float), column sums of Z^2 per block.  One warp handles
-// ROWS rows at a time; lane owns ranks lane + 32 j (j < RPL).
+// Z = M W (double-float), column sums of Z^2 per block.  LPR lanes hold one
+// row (LPR = 8, 16 or 32 >= R, or 32 with RPL = 2 for R <= 64), so a warp
+// instruction covers 32 / LPR rows and one warp iteration ROWS of those;
+// lane (h, rl) owns ranks rl + LPR j (j < RPL) of its rows.  A row's sum
+// over the ranks has the same order for every LPR.
 // ---------------------------------------------------------------------------
-template <int RPL>
+template <int RPL, int LPR = 32>
 __device__ __forceinline__ void solve_body(const float* __restrict__ M,
                                            const float* __restrict__ winv, int64_t I, int R,
                                            float* __restrict__ Z, double* __restrict__ colsq_part,
                                            const int* __restrict__ err, int vb, int nvb,
                                            const uint32_t* __restrict__ mask) {
+  static_assert(LPR == 32 || RPL == 1, "narrow rows take one rank per lane");
   constexpr int ROWS = 4;
+  constexpr int RPR = 32 / LPR;         // rows side by side in one warp instruction
+  constexpr int GROUP = ROWS * RPR;     // rows per warp iteration
   __shared__ double red[ALS_THREADS / 32][32 * RPL];
   __shared__ float2 w_s[(32 * RPL) * (32 * RPL)];  // V^{-1} as (hi, lo) pairs
   if (*err) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int h = lane / LPR, rl = lane % LPR;  // row within the instruction, rank slot
   const int RR = R * R;
   for (int e = threadIdx.x; e < RR; e += ALS_THREADS) w_s[e] = make_float2(winv[e], winv[RR + e]);
   __syncthreads();
@@ -275,38 +312,39 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ M,
   df sq[RPL];
 #pragma unroll
   for (int j = 0; j < RPL; ++j) sq[j] = {0.f, 0.f};
-  for (int64_t i0 = gwarp * ROWS; i0 < I; i0 += nwarps * ROWS) {
+  for (int64_t i0 = gwarp * GROUP; i0 < I; i0 += nwarps * GROUP) {
     if (mask) {  // a group of empty rows: Z is not written (scale_body reads no Z there)
-      bool any = false;
-#pragma unroll
-      for (int q = 0; q < ROWS; ++q) any = any || (i0 + q < I && row_live(mask, i0 + q));
-      if (!any) continue;
+      // i0 is a multiple of GROUP (4, 8 or 16), so the group's bits share one
+      // word; bits past the last row are clear
+      const uint32_t bits = __ldg(&mask[i0 >> 5]) >> (i0 & 31);
+      if ((bits & ((1u << GROUP) - 1u)) == 0u) continue;
     }
     df acc[ROWS][RPL];
 #pragma unroll
     for (int q = 0; q < ROWS; ++q)
 #pragma unroll
       for (int j = 0; j < RPL; ++j) acc[q][j] = {0.f, 0.f};
-    // lane l holds M(i0 + q, l + 32 c); broadcast by shuffles below
+    // lane (h, rl) holds M(i0 + q RPR + h, rl + LPR c); broadcast by shuffles below
     float mrow[ROWS][RPL];
 #pragma unroll
     for (int q = 0; q < ROWS; ++q)
 #pragma unroll
       for (int c = 0; c < RPL; ++c) {
-        const int s = lane + 32 * c;
-        mrow[q][c] = (i0 + q < I && s < R) ? M[(i0 + q) * R + s] : 0.f;
+        const int64_t row = i0 + q * RPR + h;
+        const int s = rl + LPR * c;
+        mrow[q][c] = (row < I && s < R) ? M[row * R + s] : 0.f;
       }
 #pragma unroll
     for (int c = 0; c < RPL; ++c) {
-      const int send = min(32, R - 32 * c);
+      const int send = min(LPR, R - LPR * c);
       for (int sl = 0; sl < send; ++sl) {
-        const int s = 32 * c + sl;
+        const int s = LPR * c + sl;
         float m[ROWS];
 #pragma unroll
-        for (int q = 0; q < ROWS; ++q) m[q] = __shfl_sync(SPM_FULL_MASK, mrow[q][c], sl);
+        for (int q = 0; q < ROWS; ++q) m[q] = __shfl_sync(SPM_FULL_MASK, mrow[q][c], (lane & ~(LPR - 1)) | sl);
 #pragma unroll
         for (int j = 0; j < RPL; ++j) {
-          const int r = lane + 32 * j;
+          const int r = rl + LPR * j;
           if (r < R) {
             const float2 w = w_s[s * R + r];
 #pragma unroll
@@ -317,13 +355,14 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ M,
     }
 #pragma unroll
     for (int q = 0; q < ROWS; ++q) {
-      if (i0 + q >= I) break;
+      const int64_t row = i0 + q * RPR + h;
+      if (row >= I) break;
 #pragma unroll
       for (int j = 0; j < RPL; ++j) {
-        const int r = lane + 32 * j;
+        const int r = rl + LPR * j;
         if (r < R) {
           const float z = acc[q][j].hi + acc[q][j].lo;
-          Z[(i0 + q) * R + r] = z;
+          Z[row * R + r] = z;
           df_add_prod(sq[j], z, z);
         }
       }
@@ -332,9 +371,11 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ M,
 #pragma unroll
   for (int j = 0; j < RPL; ++j) red[warp][lane + 32 * j] = df_value(sq[j]);
   __syncthreads();
+  // column r is held by lanes r + LPR h' (h' < RPR) of every warp
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     double s = 0.0;
-    for (int w = 0; w < ALS_THREADS / 32; ++w) s += red[w][r];
+    for (int w = 0; w < ALS_THREADS / 32; ++w)
+      for (int hh = 0; hh < RPR; ++hh) s += red[w][r + LPR * hh];
     colsq_part[(int64_t)vb * R + r] = s;
   }
 }

@@ -54,12 +54,18 @@ __global__ void __launch_bounds__(ALS_THREADS)
   const int2 tv = it[blockIdx.x];
   const BatchTensor& b = bt[tv.x];
   if (!b.active) return;
-  if (b.R <= 32)
-    solve_body<1>(b.M, b.winv, b.dims[mode], b.R, b.Z, b.colsq_part, b.err, tv.y, b.nb_solve[mode],
-                  b.live[mode]);
+  if (b.R <= 8)
+    solve_body<1, 8>(b.M, b.winv, b.dims[mode], b.R, b.Z, b.colsq_part, b.err, tv.y,
+                     b.nb_solve[mode], b.live[mode]);
+  else if (b.R <= 16)
+    solve_body<1, 16>(b.M, b.winv, b.dims[mode], b.R, b.Z, b.colsq_part, b.err, tv.y,
+                      b.nb_solve[mode], b.live[mode]);
+  else if (b.R <= 32)
+    solve_body<1, 32>(b.M, b.winv, b.dims[mode], b.R, b.Z, b.colsq_part, b.err, tv.y,
+                      b.nb_solve[mode], b.live[mode]);
   else
-    solve_body<2>(b.M, b.winv, b.dims[mode], b.R, b.Z, b.colsq_part, b.err, tv.y, b.nb_solve[mode],
-                  b.live[mode]);
+    solve_body<2, 32>(b.M, b.winv, b.dims[mode], b.R, b.Z, b.colsq_part, b.err, tv.y,
+                      b.nb_solve[mode], b.live[mode]);
 }
 
 __global__ void batch_lambda_kernel(const BatchTensor* __restrict__ bt, const int2* __restrict__ it,

@@ -58,6 +58,23 @@ def test_plain_workload_five_sweeps():
     assert np.all(np.abs(fit5 - ofit5) < 1e-3), (fit5, ofit5)
 
 
+@pytest.mark.parametrize("R", [5, 8, 13, 16])
+def test_narrow_rank_rows_with_tails_and_empty_rows(R):
+    """Ranks <= 16 put 2 or 4 rows in one warp instruction of the row solve:
+    ragged ranks (lanes past R idle), row counts that are not a multiple of
+    the row group, and empty rows (Zipf coordinates on dims larger than the
+    rows the nonzeros reach) skipped by whole groups."""
+    dims, idx, vals = synth.coo_distinct((1001, 707, 333), 20000, (1.3, 1.3, None), seed=40 + R)
+    assert any(len(np.unique(c)) < n for c, n in zip(idx, dims))  # some mode has empty rows
+    Y = synth.factors(dims, R, seed=40 + R)
+    _, fac1, lam1, fit1 = gpu_als(dims, idx, vals, Y, 1)
+    ofac1, olam1, ofit1 = oracle.cpd_als(dims, idx, vals, Y, 1, prec="fp32")
+    for d in range(3):
+        assert rel(fac1[d], ofac1[d]) < 1e-4
+    assert rel(lam1, olam1) < 1e-4
+    assert abs(fit1[0] - ofit1[0]) < 1e-3
+
+
 @pytest.mark.parametrize("R,block,dims", [(3, 3, (10, 11, 12)), (4, 3, (12, 13, 14))])
 def test_exact_recovery(R, block, dims):
     """The GPU's factors reconstruct an exactly rank-R tensor (residual taken
