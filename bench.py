@@ -625,7 +625,7 @@ def run_batching(args, rank, world):
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     out = {}
-    cands = (0, 1 << 11, 1 << 13, 1 << 15, 1 << 17)
+    cands = (0, 1 << 13, 1 << 15, 1 << 17, 1 << 18, 1 << 19)
     for name, flags, dtype, s_f in (("fp32_batched", spm.SPM_FACTOR_FP32, torch.float32, 4),
                                     ("bf16_batched", spm.SPM_FACTOR_BF16, torch.bfloat16, 2)):
         plans, plan_ms = build(flags)
