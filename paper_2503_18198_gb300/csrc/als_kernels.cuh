@@ -154,11 +154,13 @@ __device__ __forceinline__ void gram_partial_body(const FT* __restrict__ Y, int6
   }
 }
 
-// G = sum over blocks of the partials (FP64, fixed order): one warp per
-// entry; virtual block vb of nvb takes every (nvb * warps)-th entry.
-// Each entry's sum has the same order in both forms as one thread (or one
-// warp, then warp_sum_strided's tree) summing it alone; GR_ENTRIES entries
-// are summed side by side so that their loads are in flight together.
+// G = sum over blocks of the partials (FP64, fixed order).  Up to
+// ALS_SERIAL_PARTIALS partials one thread sums an entry in block order;
+// beyond that one warp does (lane-strided sums, then warp_sum_strided's
+// shuffle tree, lane 0's value kept).  Virtual block vb of nvb takes its
+// share of the entries, GR_ENTRIES at a time side by side so that their
+// loads are in flight together; an entry's order of addition does not
+// depend on the launch shape.
 constexpr int GR_ENTRIES = 4;
 __device__ __forceinline__ void gram_reduce_body(const double* __restrict__ part, int nblocks,
                                                  int R, double* __restrict__ G,
