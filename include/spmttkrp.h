@@ -291,7 +291,10 @@ spm_status cpd_als_reset(spmttkrp_plan_t plan);
  * (*resident: mode copies, partitions, MTTKRP and CP-ALS workspace; equals
  * spmttkrp_plan_bytes of such a plan) and the most its build adds for a while
  * on top (*transient, may be NULL: the sort scratch).  Factors, lambda and
- * fit buffers are the caller's and not included.  Host only. */
+ * fit buffers are the caller's and not included.  Host only; with
+ * SPM_KAPPA(0) in flags the partition count comes from the current device's
+ * SM count (SPM_ERR_CUDA when there is no device), with an explicit kappa no
+ * device is touched. */
 spm_status spmttkrp_plan_bytes_estimate(int nmodes, const int64_t *dims, int64_t nnz,
                                         int rank, uint32_t flags, size_t *resident,
                                         size_t *transient);

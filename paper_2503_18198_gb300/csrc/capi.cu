@@ -227,6 +227,7 @@ spm_status spmttkrp_plan_bytes_estimate(int nmodes, const int64_t* dims, int64_t
     return SPM_ERR_INVALID_ARG;
   int kappa = (int)SPM_KAPPA_OF(flags);
   if (kappa == 0) kappa = default_kappa();
+  if (kappa < 1) return SPM_ERR_CUDA;  // SPM_KAPPA(0) needs a device to count its SMs
   size_t tr = 0;
   plan_bytes_estimate(nmodes, dims, nnz, rank, kappa, true, (flags & SPM_PLAN_LEAN) != 0, resident,
                       &tr);
