@@ -385,6 +385,7 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world)
     e2e_value = replica_value(sum(B), e2e_ms, world)
+    copy_rates = host_copy_rates(hY[0], hout[0], stream)
 
     # one CP-ALS sweep (P6 included) on the same plan, beside the step
     lam = torch.empty(R, dtype=torch.float64, device="cuda")
@@ -425,7 +426,8 @@ def main():
                          "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                    "host_copy_GBs": copy_rates},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "plan_ms": plan_ms,
@@ -935,6 +937,32 @@ def run_precision(args, rank, world):
             sum(arms["fp32"]["mttkrp_ms_per_mode"]) / sum(arms["bf16"]["mttkrp_ms_per_mode"]),
         "clocks": clk}
     print(json.dumps(line), flush=True)
+
+
+def host_copy_rates(h_in, h_out, stream):
+    """This box's plain copy rates between pinned host memory and the device
+    (one copy of the largest factor each way, after one untimed copy): the
+    end-to-end figure depends on them.  None if the measurement fails."""
+    import torch
+    try:
+        d_in = torch.empty_like(h_in, device="cuda")
+        d_out = torch.empty_like(h_out, device="cuda")
+        rates = {}
+        for name, dst, src, n in (("h2d", d_in, h_in, h_in.numel() * 4),
+                                  ("d2h", h_out, d_out, h_out.numel() * 4)):
+            with torch.cuda.stream(stream):
+                dst.copy_(src, non_blocking=True)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                dst.copy_(src, non_blocking=True)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            rates[name] = round(n / (e0.elapsed_time(e1) * 1e-3) / 1e9, 1)
+        del d_in, d_out
+        return rates
+    except Exception:  # a context report only: never fail the bench line for it
+        return None
 
 
 KERNEL_SOURCES = ("mttkrp_kernel.cuh", "mttkrp.cu", "mttkrp_inst.cuh", "common.cuh")
