@@ -155,6 +155,31 @@ def test_bf16_factors(R):
         assert rel(outs[d], ref_fp32) < 2e-2         # includes BF16 input rounding
 
 
+@pytest.mark.parametrize("dims,R,nnz", [
+    ((3000, 200, 100), 8, 20000),       # 3 modes, R <= 32: 8-byte BF16 lanes
+    ((3000, 200, 100), 16, 20000),
+    ((3001, 203, 97), 24, 20000),       # rank not a power of two
+    ((3000, 200, 100), 32, 20000),
+    ((3000, 200, 100), 64, 20000),      # 16-byte lanes
+    ((400, 30, 3, 20, 17), 16, 6000),   # 5 modes
+    ((400, 30, 3, 20, 17), 32, 6000),
+])
+def test_bf16_factors_three_and_five_modes(dims, R, nnz):
+    """BF16 factors widen straight into FP32 pairs; element-wise parity for
+    every mode against the oracle on the same BF16 values, with Zipf heads,
+    duplicates removed, ragged tiles and empty rows."""
+    alphas = (1.1, 1.1) + (None,) * (len(dims) - 2)
+    dims, idx, vals = synth.coo_distinct(dims, nnz, alphas, seed=R + len(dims))
+    assert len(np.unique(idx[0])) < dims[0]  # mode 0 has empty rows
+    Y = synth.factors(dims, R, seed=R + len(dims))
+    plan, outs, dfac = run_all_modes(dims, idx, vals, Y, spm.SPM_FACTOR_BF16,
+                                     dtype=torch.bfloat16)
+    Yb = [f.float().cpu().numpy() for f in dfac]
+    for d in range(len(dims)):
+        assert rel(outs[d], oracle.mttkrp(dims, idx, vals, Yb, d)) < TOL, f"mode {d}"
+        assert rel(outs[d], oracle.mttkrp(dims, idx, vals, Y, d)) < 2e-2
+
+
 def test_scheme2_policy():
     g = np.random.default_rng(11)
     dims, R, nnz, kappa = (70, 60, 50), 32, 9000, 17
