@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batching", action="store_true",
+                    help="skip the batching comparison that the headline line carries")
     ap.add_argument("--workload", default="scale",
                     choices=["scale", "batching", "serving", "precision", "five", "schemes",
                              "lean"],
@@ -110,56 +112,130 @@ def algorithmic_bytes(dims, nnz, R, distinct, s_f=4):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """SM clocks and throttle reasons sampled while the GPU works.
+
+    NVML (the driver's libnvidia-ml, read through ctypes) is polled every
+    ~2 ms from a thread, so that even a timed region of a few tens of
+    milliseconds holds many samples; mark() brackets the timed region and
+    stop() summarises the samples inside it.  Falls back to nvidia-smi at
+    its own 200 ms period when NVML cannot be loaded.  Only reads settings."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # clock event reason bits of nvml.h
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+    PERIOD_S = 0.002
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.thread = None
         self.lines = []
+        self.samples = []  # (t, sm_mhz, max_mhz, reasons bits)
+        self.window = None
+        self.source = None
+        self._stop = threading.Event()
+
+    def _nvml_handle(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        uuid = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.gpu).uuid)
+        except Exception:
+            uuid = None
+        if uuid:
+            u = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            if lib.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(h)) == 0:
+                return lib, h
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(h)) != 0:
+            raise OSError("no NVML handle")
+        return lib, h
+
+    def _poll_nvml(self, lib, h):
+        import ctypes
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self._stop.is_set():
+            ok = (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and
+                  lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0)
+            r = get_reasons(h, ctypes.byref(rs)) == 0
+            if ok:
+                self.samples.append((time.perf_counter(), float(clk.value), float(mx.value),
+                                     int(rs.value) if r else 0))
+            time.sleep(self.PERIOD_S)
 
     def start(self):
+        try:
+            lib, h = self._nvml_handle()
+            self.source = "nvml"
+            self.thread = threading.Thread(target=self._poll_nvml, args=(lib, h), daemon=True)
+            self.thread.start()
+            return
+        except Exception:
+            pass
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi"
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
             self.proc = None
 
     def _read(self):
+        names = [0x8, 0x40, 0x20, 0x4]
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
-    def stop(self):
-        if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
+            f = [x.strip() for x in line.strip().split(",")]
             if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                sm, mx = float(f[1]), float(f[2])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
+            bits = sum(b for b, v in zip(names, f[5:9]) if v.lower() == "active")
+            self.samples.append((time.perf_counter(), sm, mx, bits))
+
+    def mark(self, t0, t1):
+        """Host times (perf_counter) that bracket the timed region."""
+        self.window = (t0, t1)
+
+    def stop(self):
+        self._stop.set()
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        if not self.source:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock query unavailable"],
+                    "samples": 0}
+        sel = self.samples
+        if self.window:
+            t0, t1 = self.window
+            inside = [x for x in self.samples if t0 <= x[0] <= t1]
+            sel = inside or sel
+        sm = [x[1] for x in sel]
+        mx = [x[2] for x in sel]
+        bits = 0
+        for x in sel:
+            bits |= x[3]
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(n for b, n in self.REASONS.items() if bits & b),
+                "samples": len(sm), "source": self.source,
+                "window": "timed region" if self.window else "whole run"}
 
 
 def measured_peak():
@@ -208,19 +284,46 @@ def host_info():
     return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
 
 
+def time_oracle_omp(dims, h_idx, h_vals, h_Y, R):
+    """One pass of the all-core OpenMP oracle over all modes; returns
+    (seconds, bytes, threads used)."""
+    import numpy as np
+    import oracle
+    n = h_vals.size
+    distinct = [int(np.unique(c).size) for c in h_idx]
+    t0 = time.perf_counter()
+    used = 0
+    for d in range(len(dims)):
+        _, used = oracle.mttkrp_omp(dims, h_idx, h_vals, h_Y, d)
+    dt = time.perf_counter() - t0
+    return dt, sum(algorithmic_bytes(dims, n, R, distinct)), used
+
+
 def cpu_baseline(dims, idx, vals, Y, R, target_s):
     """The oracle as it stands, single-threaded, on a prefix sample of the
-    workload's nonzeros (the same tensor's first nonzeros in draw order)."""
+    workload's nonzeros (the same tensor's first nonzeros in draw order), and
+    beside it the same definition on all host cores (OpenMP, thread-private
+    outputs added at the end) on the same sample."""
     probe = 1_000_000
     h = host_sample(dims, idx, vals, Y, probe)
     dt, _ = time_oracle(dims, *h, R)
     n = int(min(vals.numel(), max(probe, probe * target_s / max(dt, 1e-3))))
     h = host_sample(dims, idx, vals, Y, n)
     dt, b = time_oracle(dims, *h, R)
-    return {"value": b / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {n} of the workload's nonzeros (draw order), all 3 modes, "
-                      f"{dt:.1f} s single-threaded FP64",
-            "host": host_info()}
+    sample = f"first {n} of the workload's nonzeros (draw order), all 3 modes"
+    res = {"value": b / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{sample}, {dt:.1f} s single-threaded FP64",
+           "host": host_info()}
+    try:
+        time_oracle_omp(dims, *host_sample(dims, idx, vals, Y, 100_000), R)  # warm-up
+        dto, bo, used = time_oracle_omp(dims, *h, R)
+        res["openmp_all_cores"] = {"value": bo / dto / 1e9, "unit": UNIT, "cores": used,
+                                   "kind": "oracle (OpenMP, thread-private outputs)",
+                                   "sample": f"{sample}, {dto:.2f} s on {used} threads FP64",
+                                   "speedup_vs_single_thread": dt / dto}
+    except Exception as e:  # a baseline report: never fail the bench line for it
+        res["openmp_all_cores"] = {"unavailable": str(e)[:200]}
+    return res
 
 
 def arm_config(nnz, dims, R, world):
@@ -331,6 +434,7 @@ def main():
     barrier(world)
     torch.cuda.synchronize()
     per_mode = [0.0] * N
+    t_begin = time.perf_counter()
     for _ in range(args.steps):
         flush.zero_()  # evict L2 between steps (outside the events)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -340,6 +444,7 @@ def main():
         for d in range(N):
             per_mode[d] += evs[d][0].elapsed_time(evs[d][1])
     torch.cuda.synchronize()
+    clocks.mark(t_begin, time.perf_counter())
     barrier(world)
     clk = clocks.stop()
     step_ms = sum(per_mode) / args.steps
@@ -407,6 +512,30 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(dims, idx, vals, Y, R, args.cpu_seconds)
 
+    # the benchmark spec's second target beside the headline: BF16 batched CP-ALS
+    # against the tuned plain per-tensor FP32 path on the 512-tensor workload
+    batching = None
+    if rank == 0 and world == 1 and not args.no_batching:
+        del outs, flush, hY, hout, fac
+        torch.cuda.empty_cache()
+        res = batching_measure(args.tensors, args.sweeps)
+        arms = res["arms"]
+        batching = {
+            "workload": "512 independent 3-mode COO tensors (dims log-uniform [100, 20000], "
+                        "nnz log-uniform [1e3, 2e6]), R in {16, 32}, 20 CP-ALS sweeps each",
+            "metric": "CPD solves/s", "unit": "solves/s",
+            "bf16_batched": arms["bf16_batched"]["solves_per_s"],
+            "fp32_batched": arms["fp32_batched"]["solves_per_s"],
+            "fp32_per_tensor_tuned": arms["fp32_per_tensor"]["solves_per_s"],
+            "speedup_bf16_batched_vs_fp32_per_tensor": res["speedup_bf16_batched_vs_fp32_per_tensor"],
+            "fit_agreement": res["fit_agreement"],
+            "ms_per_sweep": {k: arms[k].get("ms_per_sweep") for k in ("bf16_batched", "fp32_batched")},
+            "batch_autotune_nnz_per_partition": {k: arms[k]["autotune"]["chosen"]
+                                                 for k in ("bf16_batched", "fp32_batched")},
+            "plain_kappa_autotuned": arms["fp32_per_tensor"]["kappa_autotuned"],
+            "total_nnz": res["config"]["total_nnz"], "sweeps": res["config"]["sweeps"],
+            "clocks": res["clocks"], "wall_s": round(res["wall_s"], 1)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -433,6 +562,7 @@ def main():
             "plan_ms": plan_ms,
             "als_sweep_ms": als_ms,
             "plan_bytes": spm.spmttkrp_plan_bytes(plan),
+            "batching": batching,
         }
         print(json.dumps(line), flush=True)
     plan.destroy()
@@ -574,24 +704,29 @@ def distinct_counts(idx):
     return [int(torch.unique(c).numel()) for c in idx]
 
 
-def run_batching(args, rank, world):
-    """Batching workload: many small 3-mode tensors, 20 CP-ALS sweeps each.
+def batching_measure(n_tensors, S, with_clocks=True):
+    """Batching workload: many small 3-mode tensors, S CP-ALS sweeps each.
 
     Arms (same tensors, same initial factors):
       * batched FP32 and batched BF16: spm_batch_autotune picks the
         nonzeros per partition, then one CUDA graph of a whole batched sweep
         (persistent per-class spMTTKRP launches fed by the (tensor,
-        partition) work queue, batched ALS passes) is replayed `sweeps` times;
-      * plain per-tensor FP32: cpd_als_step on each tensor in turn.
+        partition) work queue, batched ALS passes) is replayed S times;
+      * plain per-tensor FP32: cpd_als_step on each tensor in turn, each
+        tensor's partition count picked by spmttkrp_plan_autotune among the
+        batch candidates' counts and one or two partitions per SM (so the
+        comparison is batching against a tuned single-tensor path, not
+        against a default partition count).
     solves/s = tensors / time of all their sweeps (inputs resident in HBM,
-    plans built before timing).  The final fits of the BF16 batch are
-    compared with the plain FP32 path's (agreement within 1e-3)."""
+    plans built and tuned before timing).  The final fits of the batched arms
+    are compared with the plain FP32 path's (agreement within 1e-3).
+    Returns the result dict (arms, fit agreement, speedups, clocks)."""
     import numpy as np
     import torch
     import synth
     import paper_2503_18198_gb300 as spm
-    specs = synth.batching_specs(args.tensors)
-    S = args.sweeps
+    t_start = time.perf_counter()
+    specs = synth.batching_specs(n_tensors)
     tens = []
     for dims, nnz, R, seed in specs:
         dims, idx, vals = synth.tensor_torch(dims, nnz, seed, device="cuda")
@@ -599,6 +734,7 @@ def run_batching(args, rank, world):
     n = len(tens)
     total_nnz = sum(int(t[2].numel()) for t in tens)
     stream = torch.cuda.current_stream()
+    sms = spm.spm_device_sm_count()
 
     def build(flags):
         torch.cuda.synchronize()
@@ -624,8 +760,9 @@ def run_batching(args, rank, world):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
+    clocks = ClockSampler(torch.cuda.current_device()) if with_clocks else None
+    if clocks:
+        clocks.start()
     out = {}
     cands = (0, 1 << 13, 1 << 15, 1 << 17, 1 << 18, 1 << 19)
     for name, flags, dtype, s_f in (("fp32_batched", spm.SPM_FACTOR_FP32, torch.float32, 4),
@@ -662,9 +799,17 @@ def run_batching(args, rank, world):
         for p in plans:
             p.destroy()
         del facs
-    # plain per-tensor FP32 path
+    # plain per-tensor FP32 path, each plan's partition count autotuned
     plans, plan_ms = build(spm.SPM_FACTOR_FP32)
     facs = factors(torch.float32)
+    t0 = time.perf_counter()
+    chosen_k = []
+    for t, (d, _, v, R, _, _) in enumerate(tens):
+        nz = int(v.numel())
+        ks = sorted({max(1, min(65535, -(-nz // c))) for c in cands[1:]} | {sms, 2 * sms})
+        k, _ = spm.spmttkrp_plan_autotune(plans[t], facs[t], ks, reps=2)
+        chosen_k.append(k)
+    tune_ms = (time.perf_counter() - t0) * 1e3
     lams = [torch.zeros(t[3], dtype=torch.float64, device="cuda") for t in tens]
     fits = torch.zeros(n, dtype=torch.float64, device="cuda")
 
@@ -675,8 +820,14 @@ def run_batching(args, rank, world):
     ms = timed(plain)
     assert all(spm.spmttkrp_plan_status(p) == 0 for p in plans)
     out["fp32_per_tensor"] = {"solves_per_s": n / (ms * 1e-3), "ms_total": ms,
-                              "plan_build_ms": plan_ms, "fits": fits.cpu().numpy()}
-    clk = clocks.stop()
+                              "plan_build_ms": plan_ms, "autotune_ms": tune_ms,
+                              "kappa_autotuned": {"min": min(chosen_k), "max": max(chosen_k),
+                                                  "median": int(np.median(chosen_k))},
+                              "fits": fits.cpu().numpy()}
+    for p in plans:
+        p.destroy()
+    del facs
+    clk = clocks.stop() if clocks else None
     ref = out["fp32_per_tensor"]["fits"]
     agree = {}
     for name in ("fp32_batched", "bf16_batched"):
@@ -685,10 +836,7 @@ def run_batching(args, rank, world):
             "max_abs_dfit": float(dfit.max()), "within_1e-3": int((dfit <= 1e-3).sum()),
             "of": n}
     out["fp32_per_tensor"].pop("fits")
-    line = {
-        "workload": "batching", "metric": "CPD solves/s", "unit": "solves/s",
-        "value": out["bf16_batched"]["solves_per_s"], "higher_is_better": True,
-        "n_gpus": 1, "data": "synthetic",
+    return {
         "config": {"tensors": n, "total_nnz": total_nnz, "sweeps": S, "modes": 3,
                    "ranks": "16 or 32", "dims": "log-uniform [100, 20000]",
                    "nnz": "log-uniform [1e3, 2e6], at most half the cells",
@@ -696,7 +844,18 @@ def run_batching(args, rank, world):
         "arms": out, "fit_agreement": agree,
         "speedup_bf16_batched_vs_fp32_per_tensor":
             out["bf16_batched"]["solves_per_s"] / out["fp32_per_tensor"]["solves_per_s"],
-        "clocks": clk}
+        "speedup_bf16_batched_vs_fp32_batched":
+            out["bf16_batched"]["solves_per_s"] / out["fp32_batched"]["solves_per_s"],
+        "clocks": clk, "wall_s": time.perf_counter() - t_start}
+
+
+def run_batching(args, rank, world):
+    """The batching workload's own JSON line (see batching_measure)."""
+    res = batching_measure(args.tensors, args.sweeps)
+    line = {"workload": "batching", "metric": "CPD solves/s", "unit": "solves/s",
+            "value": res["arms"]["bf16_batched"]["solves_per_s"], "higher_is_better": True,
+            "n_gpus": 1, "data": "synthetic"}
+    line.update(res)
     print(json.dumps(line), flush=True)
 
 

@@ -217,6 +217,14 @@ spm_status spmttkrp_run(spmttkrp_plan_t plan, int mode,
  *  flags    SPM_FACTOR_* and SPM_KAPPA(k); work units are equal nonzero
  *           splits (no plan, so no cost-balanced partition).
  *  out      device float[dims[mode] * rank], overwritten.
+ * The records are checked on the device first (one extra read of them): an
+ * index outside its mode's range or a record whose c_d is smaller than the
+ * one before it makes the call store nothing but the cleared `out`, so bad
+ * records cannot send a gather or a store outside the caller's buffers.
+ * The call returns before the GPU has run (it does not synchronise), so such
+ * a device-side finding -- and a record-copy wait that gave up
+ * (SPM_ERR_TIMEOUT, output incomplete) -- is reported by
+ * spmttkrp_noalloc_status, not by this call's return value.
  * Its only scratch (work-unit offsets and partition boundary partials) is a
  * file-scope __device__ array of SPM_NOALLOC_SCRATCH_BYTES that every GPU
  * holds from library load to process exit; a request whose scratch would
@@ -234,6 +242,15 @@ spm_status spmttkrp_run_noalloc(int nmodes, const int64_t *dims, int64_t nnz,
                                 int mode, int rank, const void *records,
                                 const void *const *factors, uint32_t flags,
                                 float *out, void *stream);
+
+/* Synchronise `stream` and report the device-side outcome of the latest
+ * spmttkrp_run_noalloc call on the current device (the paper has no
+ * counterpart): SPM_OK, SPM_ERR_INDEX_OUT_OF_RANGE (an index outside its
+ * mode's range), SPM_ERR_INVALID_ARG (records not sorted by c_d) or
+ * SPM_ERR_TIMEOUT (a record-copy wait gave up).  It reads the error word of
+ * the same shared scratch array, so it allocates nothing either; a later
+ * call on the device replaces the outcome it reports. */
+spm_status spmttkrp_noalloc_status(void *stream);
 
 /* ---- CPD-ALS --------------------------------------------------------------- */
 
@@ -472,6 +489,18 @@ void spm_server_destroy(spm_server_t server);
  * record copies); returns SPM_ERR_TIMEOUT when the timeout was recorded, as
  * expected, with the CUDA context still usable.  Synchronises `stream`. */
 spm_status spm_selftest_wait_timeout(uint32_t limit, void *stream);
+
+/* Run the plan's spMTTKRP along `mode` (arguments as for spmttkrp_run) with
+ * the record-copy waits of its kernel set to give up at once: every warp's
+ * first wait times out, waits for the copies it already issued to land, and
+ * its block stores nothing (no output row, no boundary partial).  Returns
+ * what spmttkrp_plan_status then reports -- SPM_ERR_TIMEOUT, as expected --
+ * with the CUDA context still usable and `out` written only inside its
+ * I_mode x R rows (rows without nonzeros are zeroed, the others keep their
+ * old contents).  Synchronises `stream`.  For the failure-detection tests. */
+spm_status spm_selftest_mttkrp_timeout(spmttkrp_plan_t plan, int mode,
+                                       const void *const *factors, float *out,
+                                       void *stream);
 
 /* Fault injection on the host: the k-th device allocation made for a plan
  * from now on (k = 0: the next one) fails as if cudaMalloc had run out of

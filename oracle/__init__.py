@@ -12,12 +12,16 @@ Which passage each routine follows:
 
 * :func:`mttkrp` / :func:`mttkrp_rows` -- Sec. II-A6 (elementwise
   computation) generalised to N modes as in Algorithm 2; the output of Eq. 1
-  is a fresh matrix.
+  is a fresh matrix.  :func:`mttkrp_omp` evaluates the same definition on all
+  host cores (thread-private outputs summed at the end) for the CPU baseline.
 * :func:`mode_permutation` -- Sec. III-B2 (nonzeros ordered by the output-mode
   index); ties by the other modes in ascending mode order, then by position.
 * :func:`partition_equal` -- Sec. III-B2 (kappa equal-size partitions).
-* :func:`partition_balanced` -- Sec. III-B2's ordered nonzeros cut into
-  equal-cost work units (nonzeros plus a charge per output-row start).
+* :func:`partition_balanced` -- a design choice of this library, not a rule
+  of the paper: Sec. III-B2's ordered nonzeros cut into equal-cost work
+  units (nonzeros plus a charge per output-row start).
+* :func:`units_from_partitions` -- the equal split of each partition into
+  work units that the SCHEME1/SCHEME2 policies use (also a design choice).
 * :func:`partition_scheme1` -- Sec. III-B1 (degree-ordered cyclic deal).
 * :func:`adaptive_policy` -- Sec. III-B (I_d >= kappa selects Scheme 1).
 * :func:`cpd_als` -- Sec. II-A5 (CP-ALS over Eq. 1), standard normal-equation
@@ -62,6 +66,58 @@ def build(force: bool = False) -> str:
                            "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _SO)
     return _SO
+
+
+_SO_OMP = os.path.join(_OUT_DIR, "liboracle_omp.so")
+_lib_omp = None
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile oracle.c with -fopenmp into oracle/_lib/liboracle_omp.so (the
+    all-core CPU baseline; raises OracleError when OpenMP is unavailable)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_SO_OMP)
+            and os.path.getmtime(_SO_OMP) >= os.path.getmtime(_SRC)):
+        return _SO_OMP
+    tmp = _SO_OMP + f".tmp{os.getpid()}"
+    res = subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC",
+                          "-o", tmp, _SRC, "-lm"], capture_output=True, text=True)
+    if res.returncode != 0:
+        raise OracleError("OpenMP build of the oracle failed: " + res.stderr.strip()[-300:])
+    os.replace(tmp, _SO_OMP)
+    return _SO_OMP
+
+
+def _load_omp():
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            lib = ctypes.CDLL(build_omp())
+            P = ctypes.c_void_p
+            i64, i32 = ctypes.c_int64, ctypes.c_int
+            lib.oracle_mttkrp_omp.argtypes = [i32, P, i64, P, P, i32, P, i32, i32, P, P]
+            _lib_omp = lib
+    return _lib_omp
+
+
+def mttkrp_omp(dims, idx, vals, factors, mode, threads=0):
+    """M_mode by the same definition on `threads` OpenMP threads (0 = all)
+    with thread-private outputs added in thread order.  Returns (M, threads
+    used).  The all-core CPU baseline; not used as a parity reference."""
+    lib = _load_omp()
+    idx = _idx_list(idx)
+    vals = _f64(vals)
+    fac = [_f64(f) for f in factors]
+    R = fac[0].shape[1]
+    dims_a = np.asarray(dims, dtype=np.int64)
+    out = np.empty((int(dims[mode]), R), dtype=np.float64)
+    used = ctypes.c_int(0)
+    _check(lib.oracle_mttkrp_omp(len(idx), dims_a.ctypes.data, int(vals.size),
+                                 _ptr_array(idx), vals.ctypes.data, R, _ptr_array(fac),
+                                 int(mode), int(threads), out.ctypes.data,
+                                 ctypes.addressof(used)),
+           "oracle_mttkrp_omp")
+    return out, int(used.value)
 
 
 def _load():

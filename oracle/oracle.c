@@ -14,6 +14,9 @@
  *                        factor rows, added into row c_d of the output); the
  *                        output is a fresh matrix (Eq. 1 is a product).
  *   oracle_mttkrp_rows   the same definition restricted to chosen output rows.
+ *   oracle_mttkrp_omp    the same definition on T threads with thread-private
+ *                        outputs added in thread order (only in the OpenMP
+ *                        build; a CPU baseline, not a parity reference).
  *   oracle_mode_permutation
  *                        Sec. III-B2: nonzeros ordered by the output-mode
  *                        index; ties broken by the other modes in ascending
@@ -22,9 +25,10 @@
  *                        Sec. III-B2: kappa equal-size partitions of the
  *                        ordered nonzeros, offsets floor(z*nnz/kappa).
  *   oracle_partition_balanced
- *                        Sec. III-B2's ordered nonzeros cut into equal-cost
- *                        pieces, a nonzero costing 1 plus a fixed extra for
- *                        the first nonzero of each output row.
+ *                        a design choice of this library (not a rule of the
+ *                        paper): Sec. III-B2's ordered nonzeros cut into
+ *                        equal-cost pieces, a nonzero costing 1 plus a fixed
+ *                        extra for the first nonzero of each output row.
  *   oracle_partition_scheme1
  *                        Sec. III-B1: rows ordered by degree (descending,
  *                        ties by index), dealt cyclically to kappa partitions,
@@ -37,6 +41,7 @@
  *                        column 2-norms, and the fit 1 - |X - Xhat| / |X|.
  *
  * Build: gcc -O2 -shared -fPIC -o liboracle.so oracle.c -lm
+ *        (and with -fopenmp into liboracle_omp.so for the all-core baseline)
  */
 #include <math.h>
 #include <stdint.h>
@@ -78,6 +83,67 @@ int oracle_mttkrp(int nmodes, const int64_t *dims, int64_t nnz,
   }
   return ORACLE_OK;
 }
+
+#ifdef _OPENMP
+#include <omp.h>
+
+/* The same definition evaluated by T threads, for the all-core CPU baseline
+ * (built only into the OpenMP copy of this file, liboracle_omp.so): thread t
+ * takes the nonzeros [t*nnz/T, (t+1)*nnz/T) in input order and adds their
+ * terms into its own zeroed I_mode x R output; the T outputs are then added
+ * element by element in thread order.  Only the grouping of the FP64 sum
+ * differs from oracle_mttkrp.  nthreads <= 0 uses the OpenMP default;
+ * *threads_used receives the number of threads that ran. */
+int oracle_mttkrp_omp(int nmodes, const int64_t *dims, int64_t nnz,
+                      const int32_t *const *idx, const double *vals, int rank,
+                      const double *const *factors, int mode, int nthreads,
+                      double *out, int *threads_used) {
+  if (nmodes < 1 || mode < 0 || mode >= nmodes || rank < 1 || nnz < 0)
+    return ORACLE_ERR_ARG;
+  const size_t cells = (size_t)dims[mode] * (size_t)rank;
+  int T = nthreads > 0 ? nthreads : omp_get_max_threads();
+  double *priv = (double *)calloc((size_t)T * cells, sizeof(double));
+  if (!priv) return ORACLE_ERR_NOMEM;
+  int bad = 0, ran = 1;
+#pragma omp parallel num_threads(T) reduction(| : bad)
+  {
+    const int t = omp_get_thread_num(), nt = omp_get_num_threads();
+    if (t == 0) ran = nt;
+    double *o = priv + (size_t)t * cells;
+    for (int64_t k = nnz * t / nt; k < nnz * (t + 1) / nt; ++k) {
+      int ok = 1;
+      for (int w = 0; w < nmodes; ++w)
+        if (idx[w][k] < 0 || idx[w][k] >= dims[w]) ok = 0;
+      if (!ok) {
+        bad = 1;
+        continue;
+      }
+      int64_t i = idx[mode][k];
+      for (int r = 0; r < rank; ++r) {
+        double v = vals[k];
+        for (int w = 0; w < nmodes; ++w) {
+          if (w == mode) continue;
+          v *= factors[w][(int64_t)idx[w][k] * rank + r];
+        }
+        o[i * rank + r] += v;
+      }
+    }
+  }
+  if (bad) {
+    free(priv);
+    return ORACLE_ERR_INDEX;
+  }
+#pragma omp parallel for num_threads(T) schedule(static)
+  for (int64_t e = 0; e < (int64_t)cells; ++e) {
+    double acc = 0.0;
+    for (int t = 0; t < ran; ++t) acc += priv[(size_t)t * cells + (size_t)e];
+    out[e] = acc;
+  }
+  free(priv);
+  if (threads_used) *threads_used = ran;
+  return ORACLE_OK;
+}
+#endif
 
 /* The same definition for a chosen set of output rows only.
  * rows[j] (distinct, in [0, I_mode)) -> out[j*R + r]. */

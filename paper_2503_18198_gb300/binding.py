@@ -68,7 +68,7 @@ SYMBOLS = ("spmttkrp_plan", "spmttkrp_plan_bytes", "spmttkrp_plan_permutation",
            "spm_server_step", "spm_server_job", "spm_server_result", "spm_server_usage",
            "spm_server_destroy", "spm_selftest_wait_timeout", "spm_inject_alloc_failure",
            "cpd_als_reset", "spm_server_snapshot", "spm_server_resume",
-           "spmttkrp_run_all_host")
+           "spmttkrp_run_all_host", "spm_selftest_mttkrp_timeout", "spmttkrp_noalloc_status")
 
 
 def library_path() -> str:
@@ -144,6 +144,10 @@ def load(build_if_missing: bool = False):
     lib.spm_server_destroy.restype = None
     lib.spm_selftest_wait_timeout.argtypes = [u32, P]
     lib.spm_selftest_wait_timeout.restype = i32
+    lib.spm_selftest_mttkrp_timeout.argtypes = [P, i32, P, P, P]
+    lib.spm_selftest_mttkrp_timeout.restype = i32
+    lib.spmttkrp_noalloc_status.argtypes = [P]
+    lib.spmttkrp_noalloc_status.restype = i32
     lib.spm_inject_alloc_failure.argtypes = [i32]
     lib.spm_inject_alloc_failure.restype = None
     lib.spmttkrp_run_all_host.argtypes = [P, P, P, P]
@@ -575,6 +579,20 @@ class Server:
 def spm_selftest_wait_timeout(limit: int = 4096, stream=None) -> int:
     """Status of the bounded-wait self-test (SPM_ERR_TIMEOUT expected)."""
     return int(load().spm_selftest_wait_timeout(int(limit), _stream(stream)))
+
+
+def spm_selftest_mttkrp_timeout(plan, mode: int, factors, out, stream=None) -> int:
+    """Status of the plan's MTTKRP run with record-copy waits that give up at
+    once (SPM_ERR_TIMEOUT expected)."""
+    return int(load().spm_selftest_mttkrp_timeout(plan.handle, int(mode), _ptrs(list(factors)),
+                                                  ctypes.c_void_p(out.data_ptr()),
+                                                  _stream(stream)))
+
+
+def spmttkrp_noalloc_status(stream=None) -> int:
+    """Device-side outcome of the latest spmttkrp_run_noalloc call (a status
+    code; synchronises the stream)."""
+    return int(load().spmttkrp_noalloc_status(_stream(stream)))
 
 
 def spm_inject_alloc_failure(k: int):

@@ -42,6 +42,7 @@ enum : int {
   DEV_ERR_INDEX = 1,
   DEV_ERR_NUMERIC = 2,
   DEV_ERR_TIMEOUT = 4,
+  DEV_ERR_ORDER = 8,  // caller-held records not sorted by the output-mode index
 };
 
 // 128-bit streaming load that does not allocate in L1: the tensor copy is

@@ -54,6 +54,19 @@ spm_status spm_selftest_wait_timeout(uint32_t limit, void* stream) {
   return (h & spm::DEV_ERR_TIMEOUT) ? SPM_ERR_TIMEOUT : SPM_OK;
 }
 
+spm_status spm_selftest_mttkrp_timeout(spmttkrp_plan_t plan, int mode,
+                                       const void* const* factors, float* out, void* stream) {
+  if (!plan) return SPM_ERR_INVALID_ARG;
+  // Every warp's first wait on a record copy gives up without polling; the
+  // copies already issued still land (the drain waits for them), and the
+  // blocks skip their merge and stores.
+  plan->wait_limit = ~0u;
+  const spm_status st = spm::run_mttkrp(plan, mode, factors, out, static_cast<cudaStream_t>(stream));
+  plan->wait_limit = 0;
+  if (st != SPM_OK) return st;
+  return spmttkrp_plan_status(plan, stream);
+}
+
 void spm_inject_alloc_failure(int k) { spm::g_fail_alloc.store(k < 0 ? -1 : k); }
 
 }  // extern "C"

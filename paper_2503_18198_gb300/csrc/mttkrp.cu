@@ -81,6 +81,7 @@ spm_status run_mttkrp(spmttkrp_plan_s* p, int mode, const void* const* factors, 
   a.nin = p->N - 1;
   a.nu = p->nu;
   a.err = p->dev_err;
+  a.wait_limit = p->wait_limit;
   const size_t out_bytes = sizeof(float) * (size_t)a.I * (size_t)R;
   if (p->nnz == 0) {
     SPM_CUDA_TRY(cudaMemsetAsync(out, 0, out_bytes, s));

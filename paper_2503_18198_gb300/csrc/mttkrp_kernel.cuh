@@ -68,6 +68,10 @@ struct MttkrpArgs {
   float* cta_part;        // [kappa][2][R] boundary partials
   int* cta_meta;          // [kappa][4] (first row, last row, flags, 0)
   int* err;               // sticky device error flags
+  const int* guard;       // if non-null and non-zero when the block starts, the block
+                          // writes no output (a failed input check of the same call)
+  uint32_t wait_limit;    // polls of a record-copy wait before it gives up:
+                          // 0 = the default bound, ~0u = none at all (failure tests)
   int64_t nnz;
   int64_t I;              // rows of the output
   int R;                  // rank (runtime; equals the template rank when exact)
@@ -258,6 +262,7 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
 #endif
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int next_unit;
+  __shared__ int aborted;  // some warp gave up on a record copy: no merge, no stores
 
   const int R = a.R;
   const int NU = a.nu;
@@ -306,11 +311,16 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
     for (int st = 0; st < MT_STAGES; ++st) mbar_init(&bars[st], 1);
     fence_mbar_init();
   }
-  if (threadIdx.x == 0) next_unit = MT_WARPS;
+  if (threadIdx.x == 0) {
+    next_unit = MT_WARPS;
+    aborted = (a.guard && *(volatile const int*)a.guard) ? 1 : 0;
+  }
   __syncthreads();
+  const uint32_t wait_polls = a.wait_limit == 0u ? (1u << 24) : (a.wait_limit == ~0u ? 0u : a.wait_limit);
 
   int seq_issued = 0;    // ring sequence: tiles issued by this warp so far
   bool timeout = false;
+  const bool skip = aborted != 0;  // guard set: no unit is taken, no copy issued
 
   auto slot_reduce = [&](float (&x)[CPL][VEC]) {
 #pragma unroll
@@ -321,7 +331,7 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
         for (int e = 0; e < VEC; ++e) x[c][e] += __shfl_xor_sync(SPM_FULL_MASK, x[c][e], o);
   };
 
-  for (int u = warp; u < NU && !timeout;) {
+  for (int u = warp; u < NU && !timeout && !skip;) {
     const int64_t k0 = uoff[u], k1 = uoff[u + 1];
     const int lenw = (int)(k1 - k0);
     float* pf = part + (size_t)(2 * u) * R;
@@ -427,14 +437,20 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
         }
         {
           const int q = seq0 + t;
-          const bool ok = mbar_wait_bounded(&bars[q % MT_STAGES], (uint32_t)((q / MT_STAGES) & 1));
+          const bool ok = mbar_wait_bounded(&bars[q % MT_STAGES], (uint32_t)((q / MT_STAGES) & 1),
+                                            wait_polls);
           timeout = __any_sync(SPM_FULL_MASK, !ok);
         }
         if (timeout) {
-          // let every copy this warp started land before giving up
-          for (int q = seq0 + t + 1; q < seq0 + issued; ++q)
+          // let every copy this warp started (the one waited on included)
+          // land before giving up, then make the whole block skip its
+          // merge and stores: the units this warp held have no partials
+          for (int q = seq0 + t; q < seq0 + issued; ++q)
             (void)mbar_wait_bounded(&bars[q % MT_STAGES], (uint32_t)((q / MT_STAGES) & 1), 1u << 20);
-          if (lane == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
+          if (lane == 0) {
+            atomicOr(a.err, DEV_ERR_TIMEOUT);
+            atomicExch(&aborted, 1);
+          }
           break;
         }
         const unsigned char* stage_t = stages + ((seq0 + t) % MT_STAGES) * tile_bytes;
@@ -830,7 +846,7 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
   // group's total on its last entry.
   int* meta = a.cta_meta + 4 * z;
   const int64_t len = K1 - K0;
-  if (len == 0) {
+  if (len == 0 || aborted) {
     if (threadIdx.x == 0) { meta[0] = -1; meta[1] = -1; meta[2] = META_EMPTY; meta[3] = 0; }
     return;
   }

@@ -21,7 +21,8 @@ spm_status launch_mttkrp_fixup(const float* cta_part, const int* cta_meta, int k
 
 namespace {
 
-// The shared scratch: [work-unit offsets][boundary partials][partition meta].
+// The shared scratch: [error word][work-unit offsets][boundary partials]
+// [partition meta].
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SPM_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
@@ -53,6 +54,34 @@ __global__ void equal_units_kernel(int64_t nnz, int64_t P, int64_t* __restrict__
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= P;
        j += (int64_t)gridDim.x * blockDim.x)
     woff[j] = (j * nnz) / P;
+}
+
+struct RecordCheck {
+  int32_t lim[SPM_MAX_MODES];  // dims in record word order (output mode first)
+  int nwords;                  // index words per record (N)
+  int ri;                      // 16-byte words per record
+};
+
+// The caller's records before the MTTKRP reads them: every index inside its
+// mode's range (else DEV_ERR_INDEX) and output-mode indices non-decreasing
+// (else DEV_ERR_ORDER).  The MTTKRP blocks read the flags first and store
+// nothing when one is set, so bad records cannot send a gather or a store
+// outside the caller's buffers.
+__global__ void check_records_kernel(const int4* __restrict__ rec, int64_t nnz, RecordCheck c,
+                                     int* __restrict__ err) {
+  int bad = 0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int* w = reinterpret_cast<const int*>(rec + k * c.ri);
+    for (int j = 0; j < c.nwords; ++j) {
+      const int v = __ldg(w + j);
+      if (v < 0 || v >= c.lim[j]) bad |= DEV_ERR_INDEX;
+    }
+    if (k > 0 && __ldg(reinterpret_cast<const int*>(rec + (k - 1) * c.ri)) > __ldg(w))
+      bad |= DEV_ERR_ORDER;
+  }
+  bad = __reduce_or_sync(SPM_FULL_MASK, bad);
+  if (bad && (threadIdx.x & 31) == 0) atomicOr(err, bad);
 }
 
 }  // namespace
@@ -92,18 +121,33 @@ extern "C" spm_status spmttkrp_run_noalloc(int nmodes, const int64_t* dims, int6
     return SPM_ERR_UNSUPPORTED;
   unsigned char* scratch = nullptr;
   SPM_TRY(scratch_address(&scratch));
-  int64_t* woff = reinterpret_cast<int64_t*>(scratch);
-  float* cta_part = reinterpret_cast<float*>(scratch + woff_bytes);
-  int* cta_meta = reinterpret_cast<int*>(scratch + woff_bytes + part_bytes);
-  int* err = reinterpret_cast<int*>(scratch + woff_bytes + part_bytes + meta_bytes);
+  // layout: [error word, 256 bytes][work-unit offsets][boundary partials][meta]
+  int* err = reinterpret_cast<int*>(scratch);
+  int64_t* woff = reinterpret_cast<int64_t*>(scratch + 256);
+  float* cta_part = reinterpret_cast<float*>(scratch + 256 + woff_bytes);
+  int* cta_meta = reinterpret_cast<int*>(scratch + 256 + woff_bytes + part_bytes);
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t out_bytes = sizeof(float) * (size_t)dims[mode] * (size_t)rank;
+  // the error word starts clear for every call (spmttkrp_noalloc_status
+  // reports the latest call's); every other scratch byte the kernels read is
+  // written first by this call
+  SPM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   // rows without nonzeros must read zero; every other row is overwritten
   SPM_CUDA_TRY(cudaMemsetAsync(out, 0, out_bytes, s));
   if (nnz == 0) return SPM_OK;
-  // every other scratch byte the kernels read is written first by this call
-  SPM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+  {
+    RecordCheck chk{};
+    chk.lim[0] = (int32_t)dims[mode];
+    int j = 1;
+    for (int w = 0; w < nmodes; ++w)
+      if (w != mode) chk.lim[j++] = (int32_t)dims[w];
+    chk.nwords = nmodes;
+    chk.ri = record_int4s(nmodes);
+    const int blocks = (int)std::min<int64_t>(ceil_div<int64_t>(nnz, 256), 152 * 8);
+    check_records_kernel<<<blocks, 256, 0, s>>>(static_cast<const int4*>(records), nnz, chk, err);
+    SPM_CUDA_TRY(cudaGetLastError());
+  }
   equal_units_kernel<<<(int)std::min<int64_t>(ceil_div<int64_t>(P + 1, 256), 1024), 256, 0, s>>>(
       nnz, P, woff);
   SPM_CUDA_TRY(cudaGetLastError());
@@ -122,11 +166,25 @@ extern "C" spm_status spmttkrp_run_noalloc(int nmodes, const int64_t* dims, int6
   a.R = rank;
   a.nin = nmodes - 1;
   a.nu = nu;
-  a.err = err;  // a bounded-wait timeout flag lands here; this entry does not read it
+  a.err = err;    // read back by spmttkrp_noalloc_status
+  a.guard = err;  // set by the record check: the blocks store nothing
   MttkrpKernelFn fn = pick_mttkrp(bf16, nmodes - 1, rank);
   const size_t smem = mttkrp_smem_bytes(rank, record_int4s(nmodes), nu, bf16 ? 2 : 4);
   SPM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   fn<<<kappa, MT_THREADS, smem, s>>>(a);
   SPM_CUDA_TRY(cudaGetLastError());
   return launch_mttkrp_fixup(cta_part, cta_meta, kappa, rank, out, s);
+}
+
+extern "C" spm_status spmttkrp_noalloc_status(void* stream) {
+  unsigned char* scratch = nullptr;
+  SPM_TRY(scratch_address(&scratch));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  SPM_CUDA_TRY(cudaMemcpyAsync(&h, scratch, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SPM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h & DEV_ERR_INDEX) return SPM_ERR_INDEX_OUT_OF_RANGE;
+  if (h & DEV_ERR_ORDER) return SPM_ERR_INVALID_ARG;
+  if (h & DEV_ERR_TIMEOUT) return SPM_ERR_TIMEOUT;
+  return SPM_OK;
 }

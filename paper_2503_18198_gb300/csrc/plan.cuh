@@ -59,6 +59,9 @@ struct spmttkrp_plan_s {
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
   cudaEvent_t ev[2 * SPM_MAX_MODES + 2] = {};
   size_t bytes = 0;
+  // record-copy wait bound of the MTTKRP kernel (0 = default; failure tests
+  // set ~0u so the first wait gives up at once)
+  uint32_t wait_limit = 0;
   // allocation bookkeeping
   void* allocs[64] = {};
   size_t alloc_bytes[64] = {};

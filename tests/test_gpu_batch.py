@@ -155,6 +155,32 @@ def test_batch_matches_oracle_fit_and_factors():
     assert np.linalg.norm(lam - olam) / np.linalg.norm(olam) < 1e-4
 
 
+def test_bf16_batch_matches_oracle():
+    """BF16-stored factors in a batch of mixed tensors: the 3- and the 4-mode
+    member after two sweeps against the oracle's CP-ALS on the same
+    BF16-rounded initial factors (fit within 1e-3; factors and lambda within
+    2e-3, the BF16 storage rounding -- see the served-job test)."""
+    sel = [MIX[1], MIX[2], MIX[6]]
+    plans, facs, inputs = [], [], []
+    for dims, nnz, R, seed in sel:
+        plan, idx, vals = make_plan(dims, nnz, R, seed, spm.SPM_FACTOR_BF16)
+        plans.append(plan)
+        facs.append(init_factors(dims, R, seed, torch.bfloat16))
+        inputs.append((dims, idx, vals, R, seed))
+    B, _, nsw = batch_run(plans, facs, 2)
+    assert nsw == [2] * len(sel)
+    for t in (0, 1):
+        dims, idx, vals, R, seed = inputs[t]
+        Y0 = synth.factors(dims, R, seed=100 + seed)
+        ofac, olam, ofit = oracle.cpd_als(dims, idx, vals, Y0, 2, prec="bf16")
+        assert abs(B.fits[t].item() - ofit[-1]) < 1e-3
+        for w in range(len(dims)):
+            g = facs[t][w].double().cpu().numpy()
+            assert np.linalg.norm(g - ofac[w]) / np.linalg.norm(ofac[w]) < 2e-3, (t, w)
+        lam = B.lam(t).cpu().numpy()
+        assert np.linalg.norm(lam - olam) / np.linalg.norm(olam) < 2e-3
+
+
 def test_device_side_convergence_and_graph_replay():
     """Tensors stop independently once their fit changes by less than tol;
     the replayed graph of one sweep skips converged tensors on the device.

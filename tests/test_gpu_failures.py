@@ -2,7 +2,8 @@
 
 * A bounded device-side wait that nothing completes gives up, records a
   timeout that the host reads as SPM_ERR_TIMEOUT, and the context stays
-  usable (the same bounded wait guards the MTTKRP kernel's record copies).
+  usable; the MTTKRP kernel's own record-copy waits, made to give up at
+  once, leave every copy landed and no store outside (or inside) the output.
 * Allocation failures are injected on the host (a fake of the failing
   cudaMalloc): every allocation point of a plan returns SPM_ERR_OOM cleanly,
   without leaking device memory, and the next plan succeeds.
@@ -14,6 +15,7 @@ import pytest
 
 import oracle
 import synth
+from parity_util import check_mode_elementwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -52,6 +54,40 @@ def test_bounded_wait_times_out_and_context_stays_usable():
     ref = oracle.mttkrp(dims, idx, vals, Y, 0)
     assert np.linalg.norm(out.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-5
     assert spm.spmttkrp_plan_status(plan) == 0
+
+
+@pytest.mark.parametrize("dims,R,alphas,kappa", [
+    ((3000, 2000, 500), 32, (1.2, 1.2, 1.2), 0),      # default plan, Zipf heads
+    ((400, 300, 200, 24), 16, (1.0, 1.0, None, None), 37),
+])
+def test_mttkrp_kernel_wait_timeout_stores_nothing(dims, R, alphas, kappa):
+    """The MTTKRP kernel's own record-copy waits made to give up at once
+    (no poll at all): each warp waits for the copies it already issued,
+    the block skips its merge and every store, the host reads
+    SPM_ERR_TIMEOUT, guard rows around the output keep their contents, and
+    the next ordinary run on the same plan matches the oracle."""
+    dims, idx, vals = synth.coo_distinct(dims, 150_000, alphas, seed=R)
+    Y = synth.factors(dims, R, seed=R)
+    fac = [torch.as_tensor(f).cuda() for f in Y]
+    didx = [torch.as_tensor(c).cuda() for c in idx]
+    plan = spm.spmttkrp_plan(dims, didx, torch.as_tensor(vals).cuda(), R, spm.SPM_KAPPA(kappa))
+    G = 64  # guard rows before and after the output
+    for d in range(len(dims)):
+        buf = torch.full((dims[d] + 2 * G, R), 7.0, device="cuda")
+        out = buf[G:G + dims[d]]
+        assert spm.binding.spm_selftest_mttkrp_timeout(plan, d, fac, out) == SPM_ERR_TIMEOUT
+        torch.cuda.synchronize()
+        assert torch.all(buf[:G] == 7.0) and torch.all(buf[G + dims[d]:] == 7.0)
+        got = out.cpu().numpy()
+        nonempty = np.bincount(idx[d], minlength=dims[d]) > 0
+        assert np.all(got[~nonempty] == 0.0)  # the empty-row clear still ran
+        assert np.all(got[nonempty] == 7.0)   # no row of a timed-out block was stored
+        spm.spmttkrp_run(plan, d, fac, out)
+        assert spm.spmttkrp_plan_status(plan) == 0
+        ref = check_mode_elementwise(out.cpu().numpy(), dims, idx, vals, Y, d)
+        assert np.linalg.norm(out.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-5
+        assert torch.all(buf[:G] == 7.0) and torch.all(buf[G + dims[d]:] == 7.0)
+    plan.destroy()
 
 
 def test_injected_allocation_failures_are_clean():

@@ -18,6 +18,7 @@ import pytest
 
 import oracle
 import synth
+from parity_util import check_rows_elementwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -96,7 +97,8 @@ def run_fullsize(name, dtype, flags, check_structure):
             ref_units = oracle.partition_balanced_rows(rows_sorted, kappa * U, spm.SPM_ROW_COST)
             assert np.array_equal(units, ref_units)
         got = out.cpu().numpy()
-        ref = oracle.mttkrp_rows(dims, idx_h, vals_h, fac_h, d, rows)
+        ref = check_rows_elementwise(got[rows], dims, idx_h, vals_h, fac_h, d, rows,
+                                     what=f"{name} mode {d}")
         assert rel(got[rows], ref) < TOL, f"{name} mode {d}"
         heavy = rows[np.argmax(np.abs(ref).sum(axis=1))]
         assert rel(got[heavy], ref[np.searchsorted(rows, heavy)]) < TOL

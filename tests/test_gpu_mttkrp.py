@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 import synth
+from parity_util import check_mode_elementwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -86,7 +87,8 @@ def test_plain_workload_all_modes():
     plan, outs, _ = run_all_modes(dims, idx, vals, Y)
     check_copies(plan, idx)
     for d in range(3):
-        assert rel(outs[d], oracle.mttkrp(dims, idx, vals, Y, d)) < TOL
+        ref = check_mode_elementwise(outs[d], dims, idx, vals, Y, d)
+        assert rel(outs[d], ref) < TOL
 
 
 @pytest.mark.parametrize("dims,R,nnz,kappa", [
@@ -111,7 +113,8 @@ def test_random_shapes(dims, R, nnz, kappa):
     plan, outs, _ = run_all_modes(dims, idx, vals, Y, spm.SPM_KAPPA(kappa))
     check_copies(plan, idx, kappa)
     for d in range(len(dims)):
-        assert rel(outs[d], oracle.mttkrp(dims, idx, vals, Y, d)) < TOL, f"mode {d}"
+        ref = check_mode_elementwise(outs[d], dims, idx, vals, Y, d)
+        assert rel(outs[d], ref) < TOL, f"mode {d}"
 
 
 def test_heavy_row_dominated():
@@ -126,7 +129,7 @@ def test_heavy_row_dominated():
     for kappa in (152, 13):
         plan, outs, _ = run_all_modes(dims, idx, vals, Y, spm.SPM_KAPPA(kappa))
         for d in range(3):
-            ref = oracle.mttkrp(dims, idx, vals, Y, d)
+            ref = check_mode_elementwise(outs[d], dims, idx, vals, Y, d)
             assert rel(outs[d], ref) < TOL
             assert rel(outs[d][0], ref[0]) < TOL
 
@@ -137,7 +140,8 @@ def test_zipf_scale_recipe_small():
     plan, outs, _ = run_all_modes(dims, idx, vals, Y)
     check_copies(plan, idx)
     for d in range(3):
-        assert rel(outs[d], oracle.mttkrp(dims, idx, vals, Y, d)) < TOL
+        ref = check_mode_elementwise(outs[d], dims, idx, vals, Y, d)
+        assert rel(outs[d], ref) < TOL
 
 
 @pytest.mark.parametrize("R", [8, 16, 32, 64, 12])
@@ -149,7 +153,7 @@ def test_bf16_factors(R):
                                      dtype=torch.bfloat16)
     Yb = [f.float().cpu().numpy() for f in dfac]
     for d in range(4):
-        ref_same = oracle.mttkrp(dims, idx, vals, Yb, d)
+        ref_same = check_mode_elementwise(outs[d], dims, idx, vals, Yb, d)
         ref_fp32 = oracle.mttkrp(dims, idx, vals, Y, d)
         assert rel(outs[d], ref_same) < TOL          # accumulation error
         assert rel(outs[d], ref_fp32) < 2e-2         # includes BF16 input rounding
@@ -176,7 +180,8 @@ def test_bf16_factors_three_and_five_modes(dims, R, nnz):
                                      dtype=torch.bfloat16)
     Yb = [f.float().cpu().numpy() for f in dfac]
     for d in range(len(dims)):
-        assert rel(outs[d], oracle.mttkrp(dims, idx, vals, Yb, d)) < TOL, f"mode {d}"
+        ref = check_mode_elementwise(outs[d], dims, idx, vals, Yb, d)
+        assert rel(outs[d], ref) < TOL, f"mode {d}"
         assert rel(outs[d], oracle.mttkrp(dims, idx, vals, Y, d)) < 2e-2
 
 
@@ -191,7 +196,8 @@ def test_scheme2_policy():
     check_copies(plan, idx, kappa, policy="scheme2")
     for d in range(3):
         assert spm.spmttkrp_plan_scheme(plan, d) == 2
-        assert rel(outs[d], oracle.mttkrp(dims, idx, vals, Y, d)) < TOL
+        ref = check_mode_elementwise(outs[d], dims, idx, vals, Y, d)
+        assert rel(outs[d], ref) < TOL
 
 
 @pytest.mark.parametrize("policy", ["scheme1", "adaptive"])
@@ -221,7 +227,8 @@ def test_scheme1_and_adaptive(policy):
         units = torch.empty(kappa * U + 1, dtype=torch.int64, device="cuda")
         spm.spmttkrp_plan_work_units(plan, d, units)
         assert np.array_equal(units.cpu().numpy(), oracle.units_from_partitions(o1, U))
-        assert rel(outs[d], oracle.mttkrp(dims, idx, vals, Y, d)) < TOL
+        ref = check_mode_elementwise(outs[d], dims, idx, vals, Y, d)
+        assert rel(outs[d], ref) < TOL
 
 
 def test_edge_cases_empty_single_and_repeat():
@@ -234,7 +241,8 @@ def test_edge_cases_empty_single_and_repeat():
     idx = [np.array([4], np.int32), np.array([0], np.int32), np.array([2], np.int32)]
     plan, outs, _ = run_all_modes(dims, idx, np.array([2.0], np.float32), Y)
     for d in range(3):
-        assert rel(outs[d], oracle.mttkrp(dims, idx, [2.0], Y, d)) < TOL
+        ref = check_mode_elementwise(outs[d], dims, idx, [2.0], Y, d)
+        assert rel(outs[d], ref) < TOL
     # repeated calls are bitwise identical
     g = np.random.default_rng(0)
     idx = [g.integers(0, n, 3000).astype(np.int32) for n in (80, 70, 60)]
@@ -285,7 +293,8 @@ def test_repartition_keeps_copies_and_matches_oracle(policy, flag):
         for d in range(3):
             out = torch.full((dims[d], 32), float("nan"), device="cuda")
             spm.spmttkrp_run(plan, d, dfac, out)
-            assert rel(out.cpu().numpy(), oracle.mttkrp(dims, idx, vals, Y, d)) < TOL
+            ref = check_mode_elementwise(out.cpu().numpy(), dims, idx, vals, Y, d)
+            assert rel(out.cpu().numpy(), ref) < TOL
     assert spm.spmttkrp_plan_status(plan) == 0
 
 
@@ -315,7 +324,8 @@ def test_plan_autotune_picks_a_candidate_and_keeps_parity():
     for d in range(3):
         out = torch.full((dims[d], 32), float("nan"), device="cuda")
         spm.spmttkrp_run(plan, d, dfac, out)
-        assert rel(out.cpu().numpy(), oracle.mttkrp(dims, idx, vals, Y, d)) < TOL
+        ref = check_mode_elementwise(out.cpu().numpy(), dims, idx, vals, Y, d)
+        assert rel(out.cpu().numpy(), ref) < TOL
     chosen2, ms2 = spm.spmttkrp_plan_autotune(plan, dfac)  # default candidates
     assert chosen2 in (sms, 2 * sms) and len(ms2) == 2
     assert spm.spmttkrp_plan_status(plan) == 0

@@ -195,6 +195,28 @@ def test_invariants_linearity_duplicates_order_inner():
         assert rel(c, direct) < 1e-12
 
 
+def test_openmp_variant_is_the_same_sum():
+    """The all-core baseline evaluates the same definition: one thread gives
+    oracle_mttkrp's result bitwise (same terms in the same order), several
+    threads regroup the FP64 sum only; bad indices are rejected."""
+    try:
+        oracle.build_omp()
+    except oracle.OracleError as e:
+        pytest.skip(str(e))
+    dims, idx, vals = synth.coo_distinct((300, 200, 100, 7), 20000, (1.1, 1.1, None, None), seed=9)
+    Y = synth.factors(dims, 8, seed=9)
+    for d in range(4):
+        ref = oracle.mttkrp(dims, idx, vals, Y, d)
+        one, t1 = oracle.mttkrp_omp(dims, idx, vals, Y, d, threads=1)
+        assert t1 == 1 and np.array_equal(one, ref)
+        many, t = oracle.mttkrp_omp(dims, idx, vals, Y, d, threads=4)
+        assert t == 4 and rel(many, ref) < 1e-13
+    bad = [c.copy() for c in idx]
+    bad[2][5] = dims[2]
+    with pytest.raises(oracle.OracleError):
+        oracle.mttkrp_omp(dims, bad, vals, Y, 0, threads=3)
+
+
 def test_rows_subset_matches_full():
     dims, idx, vals = synth.coo_random((30, 20, 10), 500, seed=4, duplicates=True)
     Y = synth.factors(dims, 5, seed=4)
@@ -275,6 +297,38 @@ def test_partition_balanced_zero_row_cost_is_equal_split():
     for parts in (1, 5, 64, 2000):
         off = oracle.partition_balanced(idx, 1, parts, row_cost=0)
         assert np.array_equal(off, [-((-j * 997) // parts) for j in range(parts + 1)])
+
+
+@pytest.mark.parametrize("sizes,units", [
+    ([0], 4), ([10], 3), ([7, 0, 12], 7), ([5, 9, 1], 9), ([128, 129, 3000], 16),
+    ([1_000_003, 17, 0, 44_444], 128)])
+def test_units_from_partitions(sizes, units):
+    """Work units of a partition vector, pinned without the oracle's formula:
+    item k of a partition of L items belongs to unit ceil((k+1)*U/L) - 1 (the
+    largest w with w*L/U <= k), counted item by item; hence every unit starts
+    at its partition's offset plus the items of the earlier units, the sizes
+    inside a partition differ by at most one and add up to the partition
+    size."""
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    got = oracle.units_from_partitions(off, units)
+    assert got.size == (off.size - 1) * units + 1 and got[-1] == off[-1]
+    for z, L in enumerate(sizes):
+        cnt = [0] * units
+        for k in range(min(L, 3000)):
+            cnt[-((-(k + 1) * units) // L) - 1] += 1
+        mine = got[z * units:(z + 1) * units + 1]
+        sz = np.diff(mine)
+        assert mine[0] == off[z] and mine[-1] == off[z + 1]
+        assert sz.sum() == L and np.all(sz >= 0)
+        assert sz.max() - sz.min() <= 1
+        if L <= 3000:
+            assert list(sz) == cnt
+        else:  # sampled items (both ends and random ones) lie in their unit
+            ks = np.unique(np.concatenate([np.arange(50), L - 1 - np.arange(50),
+                                           np.random.default_rng(L).integers(0, L, 2000)]))
+            for k in ks:
+                w = -((-(int(k) + 1) * units) // L) - 1
+                assert mine[w] <= off[z] + k < mine[w + 1]
 
 
 @pytest.mark.parametrize("kappa", [1, 3, 5, 40])

@@ -8,12 +8,16 @@ calls it through the C ABI twice in a row (the second call reuses the shared
 scratch) and compares each result with the plan-based spmttkrp_run on the
 same tensor, within the 1e-5 relative Frobenius tolerance used by the other
 MTTKRP tests (the two paths split the nonzeros differently, so the FP32 sums
-are not bitwise equal).  This file is collected last.
+are not bitwise equal), and with the FP64 oracle element by element.  The
+caller's records are checked on the device before use: out-of-range indices
+and records out of output-row order make the call store nothing, which
+spmttkrp_noalloc_status reports.  This file is collected last.
 """
 import numpy as np
 import pytest
 
 import synth
+from parity_util import check_mode_elementwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -71,9 +75,40 @@ def test_noalloc_matches_plan_twice(shape, R, nnz, flags):
         for _ in range(2):
             out = torch.full((dims[mode], R), float("nan"), device="cuda")
             spm.spmttkrp_run_noalloc(dims, mode, R, rec, fac, out, flags)
-            torch.cuda.synchronize()
+            assert spm.binding.spmttkrp_noalloc_status() == 0
             assert rel(out.cpu().numpy(), ref.cpu().numpy()) < TOL
+        if mode == 0:
+            check_mode_elementwise(out.cpu().numpy(), dims, idx, vals, Y, mode)
     plan.destroy()
+
+
+def test_noalloc_rejects_bad_records_on_the_device():
+    """An index outside its mode's range, or records out of output-row
+    order: the call clears `out` and stores nothing else; the status query
+    reports the finding; the next valid call is unaffected."""
+    dims = (500, 300, 200)
+    dims, idx, vals = synth.coo_distinct(dims, 20_000, (1.1, 1.1, 1.1), seed=3)
+    Y = synth.factors(dims, 16, seed=3)
+    fac = [torch.as_tensor(f).cuda() for f in Y]
+    good = records_for_mode(idx, vals, 0)
+    G = 32
+    for word, value, status in ((2, dims[2], 2), (1, -1, 2), (0, dims[0] + 5, 2), (None, None, 1)):
+        rec = good.copy()
+        if word is None:  # two neighbouring records of different rows swapped
+            k = int(np.nonzero(np.diff(good[:, 0]))[0][3])
+            rec[[k, k + 1]] = rec[[k + 1, k]]
+        else:
+            rec[777, word] = value
+        buf = torch.full((dims[0] + 2 * G, 16), 3.0, device="cuda")
+        out = buf[G:G + dims[0]]
+        spm.spmttkrp_run_noalloc(dims, 0, 16, torch.as_tensor(rec).cuda(), fac, out)
+        assert spm.binding.spmttkrp_noalloc_status() == status
+        assert torch.all(out == 0.0)
+        assert torch.all(buf[:G] == 3.0) and torch.all(buf[G + dims[0]:] == 3.0)
+    out = torch.empty(dims[0], 16, device="cuda")
+    spm.spmttkrp_run_noalloc(dims, 0, 16, torch.as_tensor(good).cuda(), fac, out)
+    assert spm.binding.spmttkrp_noalloc_status() == 0
+    check_mode_elementwise(out.cpu().numpy(), dims, idx, vals, Y, 0)
 
 
 def test_noalloc_rejects_oversized_scratch():
