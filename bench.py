@@ -53,7 +53,7 @@ def parse():
                     help="skip the batching comparison that the headline line carries")
     ap.add_argument("--workload", default="scale",
                     choices=["scale", "batching", "serving", "precision", "five", "schemes",
-                             "lean"],
+                             "lean", "fibre"],
                     help="scale (default, the headline line); the others print their "
                          "own JSON line")
     ap.add_argument("--tensors", type=int, default=512, help="batching: tensor count")
@@ -395,7 +395,7 @@ def main():
         if rank == 0:  # the extra workloads run on one GPU
             {"batching": run_batching, "serving": run_serving, "precision": run_precision,
              "five": run_precision, "schemes": run_schemes,
-             "lean": run_lean}[args.workload](args, rank, world)
+             "lean": run_lean, "fibre": run_fibre}[args.workload](args, rank, world)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
@@ -624,6 +624,84 @@ def run_lean(args, rank, world):
     print(json.dumps({"workload": "lean", "metric": "plan bytes and spMTTKRP ms, full vs lean",
                       "unit": "ms", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
                       "results": out}), flush=True)
+
+
+def fibre_bytes(dims, nnz, R, distinct, nfib, s_f=4):
+    """B_d of a fibre-layout copy: 8-byte entries (one per nonzero and one per
+    fibre header), each distinct gathered row once, the output once."""
+    N = len(dims)
+    return [8 * (nnz + nfib[d]) + sum(distinct[w] * R * s_f for w in range(N) if w != d)
+            + dims[d] * R * 4 for d in range(N)]
+
+
+def run_fibre(args, rank, world):
+    """Fibre-layout copies (N1) against record copies on the 50M-nonzero scale
+    workload: spMTTKRP time per mode (L2 flushed before each timed run),
+    plan bytes, fibre counts, GB/s on each layout's own bytes and on the
+    record layout's bytes, nonzeros/s, and a sampled-row check of the fibre
+    result against the record result."""
+    import torch
+    import synth
+    import paper_2503_18198_gb300 as spm
+    dims, idx, vals, R, Y = synth.preset_torch("scale", nnz=args.nnz, device="cuda")
+    N = len(dims)
+    nnz = int(vals.numel())
+    distinct = distinct_counts(idx)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    peak, peak_kind = measured_peak()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    res, outs_all = {}, {}
+    for arm, flags in (("record", 0), ("fibre", spm.SPM_PLAN_FIBRE)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan = spm.spmttkrp_plan(dims, idx, vals, R, flags)
+        torch.cuda.synchronize()
+        plan_ms = (time.perf_counter() - t0) * 1e3
+        outs = [torch.empty(dims[d], R, device="cuda") for d in range(N)]
+        for _ in range(3):
+            for d in range(N):
+                spm.spmttkrp_run(plan, d, Y, outs[d])
+        reps = 10
+        ms = [0.0] * N
+        for _ in range(reps):
+            for d in range(N):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                spm.spmttkrp_run(plan, d, Y, outs[d])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms[d] += e0.elapsed_time(e1) / reps
+        nfib = [spm.spmttkrp_plan_fibre_count(plan, d) for d in range(N)] if flags else None
+        B_rec = algorithmic_bytes(dims, nnz, R, distinct)
+        B_own = fibre_bytes(dims, nnz, R, distinct, nfib) if flags else B_rec
+        res[arm] = {"plan_ms": plan_ms, "plan_bytes": spm.spmttkrp_plan_bytes(plan),
+                    "ms_per_mode": [round(m, 4) for m in ms], "ms_all_modes": sum(ms),
+                    "GBs_own_bytes": sum(B_own) / (sum(ms) * 1e-3) / 1e9,
+                    "GBs_record_bytes": sum(B_rec) / (sum(ms) * 1e-3) / 1e9,
+                    "roofline_frac_own_bytes": sum(B_own) / (sum(ms) * 1e-3) / 1e9 / peak,
+                    "nnz_per_s_per_mode": [round(nnz / (m * 1e-3), 1) for m in ms],
+                    "fibres_per_mode": nfib,
+                    "algorithmic_bytes_per_mode": B_own}
+        outs_all[arm] = outs
+        plan.destroy()
+    clk = clocks.stop()
+    g = torch.Generator(device="cuda").manual_seed(0)
+    diff = []
+    for d in range(N):
+        rows = torch.randint(0, dims[d], (4096,), device="cuda", generator=g)
+        a, b = outs_all["fibre"][d][rows], outs_all["record"][d][rows]
+        diff.append(float((a - b).norm() / b.norm().clamp_min(1e-30)))
+    print(json.dumps({
+        "workload": "fibre", "metric": "spMTTKRP ms per mode, fibre vs record copies",
+        "unit": "ms", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nnz": nnz, "rank": R, "l2": "flushed before each run",
+                   "peak": peak, "peak_source": peak_kind},
+        "results": res, "speedup_fibre_over_record": res["record"]["ms_all_modes"] /
+        res["fibre"]["ms_all_modes"],
+        "sampled_rows_rel_diff_fibre_vs_record": diff, "clocks": clk}), flush=True)
 
 
 SCHEME_SHAPES = [

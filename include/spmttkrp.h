@@ -106,6 +106,24 @@ typedef enum {
  * fit. */
 #define SPM_PLAN_LEAN (1u << 8)
 
+/* Fibre layout of the mode copies (3-mode tensors, ranks 16, 32 and 64, FP32
+ * or BF16 factors, BALANCED or SCHEME2 policies; otherwise
+ * SPM_ERR_UNSUPPORTED).  Each copy, still in the key order above, is grouped
+ * into fibres -- maximal runs of nonzeros sharing (c_d, c_a), a being the
+ * first input mode -- and stored as one stream of 8-byte entries: a header
+ * {c_a | 2^31, c_d} for each fibre followed by an entry {c_b, value bits} for
+ * each of its nonzeros (CSF-style, cf. the compressed formats that Sec. II
+ * contrasts with the per-mode COO copies of Sec. III-C).  The MTTKRP gathers
+ * the row Y_a(c_a) once per fibre instead of once per nonzero, and the copy
+ * takes 8 bytes per nonzero plus 8 per fibre instead of 16 per nonzero.
+ * Permutations, partitions and work units are those of the record layout
+ * (same P1 order, same P2 rule); work units per partition are 32 x 128 / R
+ * (the record layout's count at R = 32 and 64, twice it at R = 16).
+ * Results agree with the record layout within FP32 summation order.  Not
+ * for batches, servers, repartitioning or the partition autotuner
+ * (SPM_ERR_UNSUPPORTED). */
+#define SPM_PLAN_FIBRE (1u << 9)
+
 /* Number of partitions kappa.  0 (default) = SPM_PARTITIONS_PER_SM times the
  * device's SM count.  The paper assigns one partition per streaming
  * multiprocessor (Sec. III-B); on GB300 two resident waves of partition
@@ -168,6 +186,11 @@ spm_status spmttkrp_plan_permutation(spmttkrp_plan_t plan, int mode,
 spm_status spmttkrp_plan_partition(spmttkrp_plan_t plan, int mode,
                                    int64_t *off, int *kappa_out,
                                    void *stream);
+
+/* Number of fibres (distinct (c_d, c_a) pairs, a the first input mode) of the
+ * mode-`mode` copy of a plan made with SPM_PLAN_FIBRE (host int64 *nfib);
+ * SPM_ERR_UNSUPPORTED for other plans. */
+spm_status spmttkrp_plan_fibre_count(spmttkrp_plan_t plan, int mode, int64_t *nfib);
 
 /* Policy used for mode `mode` after ADAPTIVE is resolved: 1 = Scheme 1,
  * 2 = Scheme 2 (Sec. III-B), 0 = cost-balanced.  `scheme` is host. */

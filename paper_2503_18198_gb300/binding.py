@@ -27,6 +27,7 @@ SPM_ROW_COST = 16
 
 
 SPM_PLAN_LEAN = 1 << 8
+SPM_PLAN_FIBRE = 1 << 9
 
 
 def SPM_UNITS_PER_PARTITION(R: int) -> int:
@@ -68,7 +69,8 @@ SYMBOLS = ("spmttkrp_plan", "spmttkrp_plan_bytes", "spmttkrp_plan_permutation",
            "spm_server_step", "spm_server_job", "spm_server_result", "spm_server_usage",
            "spm_server_destroy", "spm_selftest_wait_timeout", "spm_inject_alloc_failure",
            "cpd_als_reset", "spm_server_snapshot", "spm_server_resume",
-           "spmttkrp_run_all_host", "spm_selftest_mttkrp_timeout", "spmttkrp_noalloc_status")
+           "spmttkrp_run_all_host", "spm_selftest_mttkrp_timeout", "spmttkrp_noalloc_status",
+           "spmttkrp_plan_fibre_count")
 
 
 def library_path() -> str:
@@ -146,6 +148,8 @@ def load(build_if_missing: bool = False):
     lib.spm_selftest_wait_timeout.restype = i32
     lib.spm_selftest_mttkrp_timeout.argtypes = [P, i32, P, P, P]
     lib.spm_selftest_mttkrp_timeout.restype = i32
+    lib.spmttkrp_plan_fibre_count.argtypes = [P, i32, P]
+    lib.spmttkrp_plan_fibre_count.restype = i32
     lib.spmttkrp_noalloc_status.argtypes = [P]
     lib.spmttkrp_noalloc_status.restype = i32
     lib.spm_inject_alloc_failure.argtypes = [i32]
@@ -292,6 +296,14 @@ def spmttkrp_plan_autotune(plan: Plan, factors, kappas=None, reps: int = 3, stre
                                          ms, _stream(stream)),
            "spmttkrp_plan_autotune")
     return int(chosen.value), list(ms)
+
+
+def spmttkrp_plan_fibre_count(plan: Plan, mode: int) -> int:
+    """Fibres (distinct (c_d, c_a) pairs) of a SPM_PLAN_FIBRE plan's mode copy."""
+    n = ctypes.c_int64()
+    _check(load().spmttkrp_plan_fibre_count(plan.handle, int(mode), ctypes.byref(n)),
+           "spmttkrp_plan_fibre_count")
+    return int(n.value)
 
 
 def spmttkrp_plan_destroy(plan: Plan):

@@ -157,7 +157,7 @@ spm_status batch_add(spm_batch_s* B, spmttkrp_plan_s* p, void* const* factors, d
       start_sweeps >= max_sweeps)
     return SPM_ERR_INVALID_ARG;
   const int kc = batch_kclass(p->N, p->R);
-  if (kc == KC_NONE || p->lean || (B->bf16 >= 0 && B->bf16 != (int)p->bf16))
+  if (kc == KC_NONE || p->lean || p->fibre || (B->bf16 >= 0 && B->bf16 != (int)p->bf16))
     return SPM_ERR_UNSUPPORTED;
   for (int d = 0; d < p->N; ++d)
     if (p->mode[d].scheme == 1) return SPM_ERR_UNSUPPORTED;
@@ -400,7 +400,7 @@ spm_status spm_batch_create(spm_batch_t* out, int ntensors, const spmttkrp_plan_
   for (int t = 0; t < ntensors; ++t) {
     const spmttkrp_plan_s* p = plans[t];
     if (!p) return SPM_ERR_INVALID_ARG;
-    if (p->bf16 != plans[0]->bf16 || p->lean || batch_kclass(p->N, p->R) == KC_NONE)
+    if (p->bf16 != plans[0]->bf16 || p->lean || p->fibre || batch_kclass(p->N, p->R) == KC_NONE)
       return SPM_ERR_UNSUPPORTED;
   }
   spm_batch_s* B = new (std::nothrow) spm_batch_s();

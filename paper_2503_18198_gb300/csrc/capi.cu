@@ -44,6 +44,20 @@ spm_status plan_realloc(spmttkrp_plan_s* p, void** ptr, size_t bytes) {
   return SPM_OK;
 }
 
+void plan_free(spmttkrp_plan_s* p, void** ptr) {
+  int i = 0;
+  while (i < p->nallocs && p->allocs[i] != *ptr) ++i;
+  if (i == p->nallocs) return;
+  cudaFree(*ptr);
+  p->bytes -= p->alloc_bytes[i];
+  for (int j = i + 1; j < p->nallocs; ++j) {
+    p->allocs[j - 1] = p->allocs[j];
+    p->alloc_bytes[j - 1] = p->alloc_bytes[j];
+  }
+  --p->nallocs;
+  *ptr = nullptr;
+}
+
 int sm_count() {
   int dev = 0, n = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -129,11 +143,19 @@ spm_status spmttkrp_plan(spmttkrp_plan_t* out, int nmodes, const int64_t* dims, 
     for (int w = 0; w < nmodes; ++w)
       if (!idx[w]) return SPM_ERR_INVALID_ARG;
   }
-  const uint32_t known = SPM_FACTOR_MASK | SPM_POLICY_MASK | SPM_PLAN_LEAN | (0xFFFFu << 16);
+  const uint32_t known =
+      SPM_FACTOR_MASK | SPM_POLICY_MASK | SPM_PLAN_LEAN | SPM_PLAN_FIBRE | (0xFFFFu << 16);
   if (flags & ~known) return SPM_ERR_INVALID_ARG;
   const int policy = (int)((flags & SPM_POLICY_MASK) >> 4);
   if (policy > 3) return SPM_ERR_INVALID_ARG;
   const bool lean = (flags & SPM_PLAN_LEAN) != 0;
+  const bool fibre = (flags & SPM_PLAN_FIBRE) != 0;
+  // the fibre layout: three modes, unit-per-slot kernel ranks, copies in the
+  // P1 order (Scheme 1 reorders them), one record layout at a time
+  if (fibre && (nmodes != 3 || fibre_slots(rank) == 0 || lean ||
+                (policy != (int)(SPM_POLICY_BALANCED >> 4) &&
+                 policy != (int)(SPM_POLICY_SCHEME2 >> 4))))
+    return SPM_ERR_UNSUPPORTED;
   // a lean plan keeps every copy in the P1 order (Scheme 1 reorders copies)
   if (lean && policy != (int)(SPM_POLICY_BALANCED >> 4) && policy != (int)(SPM_POLICY_SCHEME2 >> 4))
     return SPM_ERR_UNSUPPORTED;
@@ -152,9 +174,12 @@ spm_status spmttkrp_plan(spmttkrp_plan_t* out, int nmodes, const int64_t* dims, 
   p->flags = flags;
   p->bf16 = (flags & SPM_FACTOR_MASK) == SPM_FACTOR_BF16;
   p->lean = lean;
+  p->fibre = fibre;
   p->kappa = kappa;
   p->kappa_cap = kappa;
-  p->nu = SPM_UNITS_PER_PARTITION(rank);
+  // a fibre plan's warps take fibre_slots(R) units side by side, all 32 warps
+  // of a block once each
+  p->nu = fibre ? 32 * fibre_slots(rank) : SPM_UNITS_PER_PARTITION(rank);
   p->policy = policy;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
@@ -228,10 +253,19 @@ spm_status spmttkrp_plan_bytes_estimate(int nmodes, const int64_t* dims, int64_t
   int kappa = (int)SPM_KAPPA_OF(flags);
   if (kappa == 0) kappa = default_kappa();
   if (kappa < 1) return SPM_ERR_CUDA;  // SPM_KAPPA(0) needs a device to count its SMs
+  const bool fibre = (flags & SPM_PLAN_FIBRE) != 0;
+  if (fibre && (nmodes != 3 || fibre_slots(rank) == 0)) return SPM_ERR_UNSUPPORTED;
   size_t tr = 0;
   plan_bytes_estimate(nmodes, dims, nnz, rank, kappa, true, (flags & SPM_PLAN_LEAN) != 0, resident,
-                      &tr);
+                      &tr, fibre);
   if (transient) *transient = tr;
+  return SPM_OK;
+}
+
+spm_status spmttkrp_plan_fibre_count(spmttkrp_plan_t plan, int mode, int64_t* nfib) {
+  if (!plan || !nfib || mode < 0 || mode >= plan->N) return SPM_ERR_INVALID_ARG;
+  if (!plan->fibre) return SPM_ERR_UNSUPPORTED;
+  *nfib = plan->mode[mode].nfib;
   return SPM_OK;
 }
 
@@ -245,7 +279,8 @@ spm_status spmttkrp_plan_autotune(spmttkrp_plan_t plan, const void* const* facto
                                   const int* kappas, int nkappas, int reps, int* chosen,
                                   float* ms, void* stream) {
   if (!plan || !factors || reps < 1 || (kappas && nkappas < 1) || !chosen) return SPM_ERR_INVALID_ARG;
-  if (plan->policy != (int)(SPM_POLICY_BALANCED >> 4) && plan->policy != (int)(SPM_POLICY_SCHEME2 >> 4))
+  if (plan->fibre ||
+      (plan->policy != (int)(SPM_POLICY_BALANCED >> 4) && plan->policy != (int)(SPM_POLICY_SCHEME2 >> 4)))
     return SPM_ERR_UNSUPPORTED;
   const int sms = sm_count();
   if (sms < 1) return SPM_ERR_CUDA;

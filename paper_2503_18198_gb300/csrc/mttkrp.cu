@@ -17,6 +17,9 @@ MttkrpKernelFn pick_mttkrp_bf16_c(int R);
 MttkrpKernelFn pick_mttkrp_f32_lean(int nin, int R);
 MttkrpKernelFn pick_mttkrp_bf16_lean(int nin, int R);
 
+spm_status launch_mttkrp_fibre(spmttkrp_plan_s* p, int mode, const void* const* factors,
+                               float* out, cudaStream_t s);  // mttkrp_fibre.cu
+
 MttkrpKernelFn pick_mttkrp(bool bf16, int nin, int R) {
   if (nin == 4) return bf16 ? pick_mttkrp_bf16_c(R) : pick_mttkrp_f32_c(R);
   if (bf16) return nin <= 2 ? pick_mttkrp_bf16_a(nin, R) : pick_mttkrp_bf16_b(nin, R);
@@ -95,18 +98,22 @@ spm_status run_mttkrp(spmttkrp_plan_s* p, int mode, const void* const* factors, 
     zero_empty_rows_kernel<<<blocks, 256, 0, s>>>(c.rowmask, a.I, R, out);
     SPM_CUDA_TRY(cudaGetLastError());
   }
-  MttkrpKernelFn fn = lean ? (p->bf16 ? pick_mttkrp_bf16_lean(p->N - 1, R)
-                                      : pick_mttkrp_f32_lean(p->N - 1, R))
-                           : pick_mttkrp(p->bf16, p->N - 1, R);
-  if (!fn) return SPM_ERR_UNSUPPORTED;
-  const size_t smem = mttkrp_smem_bytes(R, record_int4s(p->N), p->nu, p->bf16 ? 2 : 4);
-  SPM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // Smallest shared-memory carve-out that fits: the rest of the unified
-  // array is L1 for the gathered factor rows.
-  const int carve = (int)std::min<size_t>(100, (smem + 4096) * 100 / (228 * 1024) + 1);
-  SPM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
-  fn<<<p->kappa, MT_THREADS, smem, s>>>(a);
-  SPM_CUDA_TRY(cudaGetLastError());
+  if (c.fstream) {
+    SPM_TRY(launch_mttkrp_fibre(p, mode, factors, out, s));
+  } else {
+    MttkrpKernelFn fn = lean ? (p->bf16 ? pick_mttkrp_bf16_lean(p->N - 1, R)
+                                        : pick_mttkrp_f32_lean(p->N - 1, R))
+                             : pick_mttkrp(p->bf16, p->N - 1, R);
+    if (!fn) return SPM_ERR_UNSUPPORTED;
+    const size_t smem = mttkrp_smem_bytes(R, record_int4s(p->N), p->nu, p->bf16 ? 2 : 4);
+    SPM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // Smallest shared-memory carve-out that fits: the rest of the unified
+    // array is L1 for the gathered factor rows.
+    const int carve = (int)std::min<size_t>(100, (smem + 4096) * 100 / (228 * 1024) + 1);
+    SPM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+    fn<<<p->kappa, MT_THREADS, smem, s>>>(a);
+    SPM_CUDA_TRY(cudaGetLastError());
+  }
   if (c.scheme != 1 && p->kappa > 1) {
     const int threads = 256;
     const int blocks = (int)ceil_div<int64_t>((int64_t)p->kappa * 32, threads);

@@ -836,11 +836,11 @@ spm_status build_copies_t(spmttkrp_plan_s* p, const int32_t* const* idx_in, cons
 }  // namespace
 
 void plan_bytes_estimate(int N, const int64_t* dims, int64_t nnz, int R, int kappa, bool als,
-                         bool lean, size_t* resident, size_t* transient) {
+                         bool lean, size_t* resident, size_t* transient, bool fibre) {
   // mirrors the plan_alloc calls of spmttkrp_plan, build_copies and
   // ensure_als_state (each allocation of 0 bytes counts 16)
   const int RI = record_int4s(N);
-  const int nu = SPM_UNITS_PER_PARTITION(R);
+  const int nu = fibre ? 32 * fibre_slots(R) : SPM_UNITS_PER_PARTITION(R);
   const int64_t nn = nnz > 0 ? nnz : 1;
   int64_t Imax = 1;
   for (int w = 0; w < N; ++w) Imax = std::max(Imax, dims[w]);
@@ -850,6 +850,11 @@ void plan_bytes_estimate(int N, const int64_t* dims, int64_t nnz, int R, int kap
   for (int d = 0; d < N; ++d) {
     if (lean && d > 0) {
       b += sizeof(int32_t) * (size_t)nn + 16;
+    } else if (fibre) {
+      // at most one fibre per nonzero: an upper bound (the count is data-dependent)
+      b += sizeof(int2) * (size_t)(2 * (size_t)(nnz > 0 ? nnz : 0) + 2);
+      b += sizeof(FibreUnit) * (size_t)kappa * nu;
+      b += sizeof(int32_t) * (size_t)nn;
     } else {
       b += sizeof(int4) * RI * (size_t)nn + 256;
       b += sizeof(int32_t) * (size_t)nn;
@@ -872,10 +877,14 @@ void plan_bytes_estimate(int N, const int64_t* dims, int64_t nnz, int R, int kap
                sizeof(uint32_t) * RS_BINS * (size_t)ceil_div<int64_t>(cap, RS_TILE) +
                sizeof(uint32_t) * RS_BINS + sizeof(int64_t) * SPM_MAX_MODES +
                sizeof(unsigned long long) * SPM_MAX_MODES;
+  if (fibre)  // the record copies live until every fibre stream is built
+    *transient = std::max<size_t>(*transient, (sizeof(int4) * RI + 256) * (size_t)nn * N +
+                                                  sizeof(int32_t) * (size_t)nn);
 }
 
 spm_status plan_repartition(spmttkrp_plan_s* p, int kappa, cudaStream_t s) {
   if (kappa < 1 || kappa > 0xFFFF) return SPM_ERR_INVALID_ARG;
+  if (p->fibre) return SPM_ERR_UNSUPPORTED;  // work units are baked into the fibre streams
   if (p->policy != (int)(SPM_POLICY_BALANCED >> 4) && p->policy != (int)(SPM_POLICY_SCHEME2 >> 4))
     return SPM_ERR_UNSUPPORTED;
   if (kappa == p->kappa) return SPM_OK;
@@ -913,10 +922,16 @@ spm_status plan_repartition(spmttkrp_plan_s* p, int kappa, cudaStream_t s) {
   return SPM_OK;
 }
 
+spm_status build_fibre_copies(spmttkrp_plan_s* p, cudaStream_t s);  // fibre_plan.cu
+
 spm_status build_copies(spmttkrp_plan_s* p, const int32_t* const* idx, const float* vals,
                         cudaStream_t s) {
   SPM_TRY(plan_alloc(p, (void**)&p->norm_part, sizeof(double) * NORM_BLOCKS));
-  if (record_int4s(p->N) == 1) return build_copies_t<1>(p, idx, vals, s);
+  if (record_int4s(p->N) == 1) {
+    SPM_TRY(build_copies_t<1>(p, idx, vals, s));
+    // the fibre layout is made from the finished record copies (3 modes)
+    return p->fibre ? build_fibre_copies(p, s) : SPM_OK;
+  }
   return build_copies_t<2>(p, idx, vals, s);
 }
 

@@ -4,8 +4,23 @@
 
 #include "common.cuh"
 
+// Work unit of a fibre-layout copy: its range of stream entries (from its
+// first nonzero to its last, headers between them included) and the fibre
+// header of its first nonzero, which may lie before the range.
+struct FibreUnit {
+  int64_t sbeg, send;  // stream entries [sbeg, send); empty unit: sbeg == send
+  int cd_first;        // output row of the unit's first nonzero
+  int ca_first;        // first input-mode index of that nonzero's fibre
+  int cd_last;         // output row of the nonzero before the unit's end (-1: none)
+  int pad;
+};
+
 struct spm_mode_copy {
-  int4* rec = nullptr;       // records, record_int4s(N) int4 per nonzero (null: lean copy)
+  int4* rec = nullptr;       // records, record_int4s(N) int4 per nonzero (null: lean or fibre copy)
+  int2* fstream = nullptr;   // fibre copy: header entries {c_a | 2^31, c_d} each followed by
+                             // the fibre's nonzero entries {c_b, value bits}; 2 entries of padding
+  FibreUnit* funits = nullptr;  // fibre copy: [kappa * nu] work units
+  int64_t nfib = 0;          // fibre copy: number of fibres (headers)
   int32_t* perm = nullptr;   // input position of each copy position (null: lean copy)
   int32_t* src = nullptr;    // lean copy: position in copy 0 of each copy position
   int64_t* off = nullptr;    // device int64[kappa+1] partition offsets
@@ -39,6 +54,7 @@ struct spmttkrp_plan_s {
   uint32_t flags = 0;
   bool bf16 = false;
   bool lean = false;  // SPM_PLAN_LEAN: copies 1..N-1 are positions into copy 0
+  bool fibre = false; // SPM_PLAN_FIBRE: every copy in the fibre layout (3 modes)
   int kappa = 0;
   int kappa_cap = 0;  // partitions the off/woff/cta arrays are sized for
   int nu = 0;      // work units per partition
@@ -77,11 +93,28 @@ spm_status plan_alloc(spmttkrp_plan_s* p, void** ptr, size_t bytes);
 // (contents not kept).
 spm_status plan_realloc(spmttkrp_plan_s* p, void** ptr, size_t bytes);
 
+// Release one allocation made by plan_alloc (after a device synchronisation
+// of the caller's stream, or stream-ordered work that no longer reads it).
+void plan_free(spmttkrp_plan_s* p, void** ptr);
+
+// Slots (work units a warp takes side by side) of the fibre-layout kernel for
+// rank R: each lane holds SPM_FB_VEC ranks of a unit's rows (4: one 16-byte
+// FP32 or 8-byte BF16 load per row; 8: two 16-byte FP32 loads or one 16-byte
+// BF16 load), R / SPM_FB_VEC lanes per unit; 0 when the rank has no fibre
+// kernel.  With 8 the per-step control work is shared by twice the slots but
+// a batch more often holds a row change; 4 measured faster.
+#ifndef SPM_FB_VEC
+#define SPM_FB_VEC 4
+#endif
+inline int fibre_slots(int R) {
+  return (R == 16 || R == 32 || R == 64) ? 32 * SPM_FB_VEC / R : 0;
+}
+
 // Device bytes a plan holds (resident: copies, partitions, workspace, and
 // with `als` the CP-ALS state) and the most its build adds for a while
 // (transient scratch), for the given shape.
 void plan_bytes_estimate(int N, const int64_t* dims, int64_t nnz, int R, int kappa, bool als,
-                         bool lean, size_t* resident, size_t* transient);
+                         bool lean, size_t* resident, size_t* transient, bool fibre = false);
 
 // P2 again for a new partition count (cost-balanced and Scheme 2 policies).
 spm_status plan_repartition(spmttkrp_plan_s* p, int kappa, cudaStream_t s);

@@ -58,7 +58,13 @@ def test_invalid_arguments_rejected_on_host():
     bad = (ctypes.c_int64 * 3)(4, 0, 4)
     assert lib.spmttkrp_plan(ctypes.byref(h), 3, bad, 0, None, None, 4, 0, None) == 1
     # unknown flag bits
-    assert lib.spmttkrp_plan(ctypes.byref(h), 3, dims, 0, None, None, 4, 1 << 9, None) == 1
+    assert lib.spmttkrp_plan(ctypes.byref(h), 3, dims, 0, None, None, 4, 1 << 10, None) == 1
+    # the fibre layout outside its shapes: rank 4, four modes (SPM_ERR_UNSUPPORTED)
+    assert lib.spmttkrp_plan(ctypes.byref(h), 3, dims, 0, None, None, 4, spm.SPM_PLAN_FIBRE,
+                             None) == 7
+    dims4 = (ctypes.c_int64 * 4)(4, 4, 4, 4)
+    assert lib.spmttkrp_plan(ctypes.byref(h), 4, dims4, 0, None, None, 32, spm.SPM_PLAN_FIBRE,
+                             None) == 7
     # null plan handles
     assert lib.spmttkrp_run(None, 0, None, None, None) == 1
     assert lib.cpd_als_step(None, None, None, None, None) == 1
