@@ -17,7 +17,7 @@
 // error-free FP32 transformations (two-product via FMA, two-sum) instead.
 #include <algorithm>
 
-#include "als_kernels.cuh"
+#include "als_tc.cuh"
 
 namespace spm {
 namespace {
@@ -46,6 +46,14 @@ __global__ void __launch_bounds__(ALS_THREADS)
                  float* __restrict__ Z, double* __restrict__ colsq_part,
                  const int* __restrict__ err, const uint32_t* __restrict__ mask) {
   solve_body<RPL, LPR>(M, winv, I, R, Z, colsq_part, err, blockIdx.x, gridDim.x, mask);
+}
+
+template <int R>
+__global__ void __launch_bounds__(TC_THREADS)
+    tc_solve_kernel(const float* __restrict__ M, const double* __restrict__ W, int64_t I,
+                    float* __restrict__ Z, double* __restrict__ colsq_part,
+                    const int* __restrict__ err, int nvb, const uint32_t* __restrict__ mask) {
+  tc_solve_body<R>(M, W, I, Z, colsq_part, err, blockIdx.x, nvb, mask);
 }
 
 __global__ void lambda_kernel(const double* __restrict__ colsq_part, int nblocks, int R,
@@ -95,6 +103,49 @@ spm_status launch_gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, 
 }
 
 }  // namespace
+
+// The tensor-core row solve over `nb` virtual blocks (R = 16, 32 or 64).
+template <int R>
+spm_status launch_tc_solve_r(int nb, const float* M, const double* W, int64_t I, float* Z,
+                             double* colsq_part, const int* err, const uint32_t* mask,
+                             cudaStream_t s) {
+  constexpr int smem = (int)TcSolveShape<R>::SMEM;
+  SPM_CUDA_TRY(cudaFuncSetAttribute(tc_solve_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  tc_solve_kernel<R><<<nb, TC_THREADS, smem, s>>>(M, W, I, Z, colsq_part, err, nb, mask);
+  SPM_CUDA_TRY(cudaGetLastError());
+  return SPM_OK;
+}
+
+spm_status launch_tc_solve(int R, int nb, const float* M, const double* W, int64_t I, float* Z,
+                           double* colsq_part, const int* err, const uint32_t* mask,
+                           cudaStream_t s) {
+  switch (R) {
+    case 16: return launch_tc_solve_r<16>(nb, M, W, I, Z, colsq_part, err, mask, s);
+    case 32: return launch_tc_solve_r<32>(nb, M, W, I, Z, colsq_part, err, mask, s);
+    case 64: return launch_tc_solve_r<64>(nb, M, W, I, Z, colsq_part, err, mask, s);
+    default: return SPM_ERR_UNSUPPORTED;
+  }
+}
+
+// The row solve of one mode: tensor cores for R = 16, 32 and 64, else the
+// CUDA-core double-float solve in the lane layout of R.  Kept out of line:
+// inlined into the sweep loop, the equivalent if-chain launched the next
+// variant's instantiation on the aarch64 host build (gcc 13.3, -O2), which
+// the bitwise batch-versus-single sweep test exposed.
+__attribute__((noinline)) spm_status launch_solve(int R, int nb, const float* M, const float* winv,
+                                                  const double* W, int64_t I, float* Z,
+                                                  double* colsq_part, const int* err,
+                                                  const uint32_t* mask, cudaStream_t s) {
+  if (tc_solve_rank(R)) return launch_tc_solve(R, nb, M, W, I, Z, colsq_part, err, mask, s);
+  switch (R <= 8 ? 0 : R <= 16 ? 1 : R <= 32 ? 2 : 3) {
+    case 0: solve_kernel<1, 8><<<nb, ALS_THREADS, 0, s>>>(M, winv, I, R, Z, colsq_part, err, mask); break;
+    case 1: solve_kernel<1, 16><<<nb, ALS_THREADS, 0, s>>>(M, winv, I, R, Z, colsq_part, err, mask); break;
+    case 2: solve_kernel<1, 32><<<nb, ALS_THREADS, 0, s>>>(M, winv, I, R, Z, colsq_part, err, mask); break;
+    default: solve_kernel<2, 32><<<nb, ALS_THREADS, 0, s>>>(M, winv, I, R, Z, colsq_part, err, mask); break;
+  }
+  SPM_CUDA_TRY(cudaGetLastError());
+  return SPM_OK;
+}
 
 spm_status gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, cudaStream_t s,
                 const uint32_t* mask) {
@@ -148,14 +199,7 @@ spm_status als_sweep(spmttkrp_plan_s* p, void* const* factors, double* lambda, d
     const int nb = als_row_blocks(I, nb_solve);
     // rows without nonzeros in mode d have a zero update: passes skip them
     const uint32_t* live = p->mode[d].empty_rows > 0 ? p->mode[d].rowmask : nullptr;
-    if (R <= 8)
-      solve_kernel<1, 8><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err, live);
-    else if (R <= 16)
-      solve_kernel<1, 16><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err, live);
-    else if (R <= 32)
-      solve_kernel<1, 32><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err, live);
-    else
-      solve_kernel<2, 32><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, p->dev_err, live);
+    SPM_TRY(launch_solve(R, nb, A.M, A.winv, A.chol, I, A.Z, A.colsq_part, p->dev_err, live, s));
     lambda_kernel<<<1, 256, 0, s>>>(A.colsq_part, nb, R, A.lambda_ws, p->dev_err);
     const bool last = d == N - 1;
     const int nbs = als_row_blocks(I, nb_solve);

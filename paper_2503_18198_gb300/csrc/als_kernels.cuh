@@ -21,29 +21,33 @@ constexpr int GRAM_TILE_ROWS = 32;
 constexpr int ALS_MIN_ROWS = 256;
 
 // ---- double-float helpers (Dekker / Knuth error-free transformations) ----
+// Every operation is an explicitly rounded intrinsic: the compiler may not
+// contract a multiply and an add into one FMA, so the bits do not depend on
+// which kernel (or translation unit) the code is compiled into -- a tensor's
+// batched and single-tensor sweeps must agree bitwise.
 struct df {
   float hi, lo;
 };
 __device__ __forceinline__ void df_add_prod(df& acc, float a, float b) {
-  const float p = a * b;
+  const float p = __fmul_rn(a, b);
   const float e = fmaf(a, b, -p);  // exact: a*b = p + e
-  const float s = acc.hi + p;
-  const float bb = s - acc.hi;
-  const float err = (acc.hi - (s - bb)) + (p - bb);
+  const float s = __fadd_rn(acc.hi, p);
+  const float bb = __fsub_rn(s, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
   acc.hi = s;
-  acc.lo += err + e;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
 }
 __device__ __forceinline__ void df_add_prod2(df& acc, float a, float bh, float bl) {
-  const float p = a * bh;
+  const float p = __fmul_rn(a, bh);
   float e = fmaf(a, bh, -p);
   e = fmaf(a, bl, e);
-  const float s = acc.hi + p;
-  const float bb = s - acc.hi;
-  const float err = (acc.hi - (s - bb)) + (p - bb);
+  const float s = __fadd_rn(acc.hi, p);
+  const float bb = __fsub_rn(s, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
   acc.hi = s;
-  acc.lo += err + e;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
 }
-__device__ __forceinline__ double df_value(const df& a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double df_value(const df& a) { return __dadd_rn((double)a.hi, (double)a.lo); }
 
 // Sum of x[0], x[stride], ..., x[(n-1) stride] by one warp in a fixed order:
 // lane l adds elements l, l + 32, ... in turn, then a fixed butterfly over the
@@ -214,9 +218,9 @@ __device__ __forceinline__ void gram_reduce_body(const double* __restrict__ part
 __device__ __forceinline__ void system_body(const double* __restrict__ grams, int N, int d, int R,
                                             double* __restrict__ V, float* __restrict__ winv,
                                             int* __restrict__ err) {
-  // The R x R working matrix lives in shared memory (R <= 64); `V` is not
-  // used (kept for the callers' argument lists).
-  (void)V;
+  // The R x R working matrix lives in shared memory (R <= 64); V^{-1} is
+  // written to `V` in FP64 (the tensor-core solve splits it) and to `winv`
+  // as FP32 hi/lo pairs (the CUDA-core solve).
   __shared__ double S[64 * 64];
   __shared__ int bad;
   if (threadIdx.x == 0) bad = *err ? 1 : 0;
@@ -226,7 +230,7 @@ __device__ __forceinline__ void system_body(const double* __restrict__ grams, in
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
     double v = 1.0;
     for (int w = 0; w < N; ++w)
-      if (w != d) v *= grams[(int64_t)w * RR + e];
+      if (w != d) v = __dmul_rn(v, grams[(int64_t)w * RR + e]);
     S[e] = v;
   }
   __syncthreads();
@@ -240,12 +244,12 @@ __device__ __forceinline__ void system_body(const double* __restrict__ grams, in
     __syncthreads();
     if (bad) break;
     const double ljj = S[j * R + j];
-    for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) S[i * R + j] /= ljj;
+    for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) S[i * R + j] = __ddiv_rn(S[i * R + j], ljj);
     __syncthreads();
     const int m = R - j - 1;  // trailing (m x m) lower triangle update
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
       const int i = j + 1 + e / m, k = j + 1 + e % m;
-      if (k <= i) S[i * R + k] -= S[i * R + j] * S[k * R + j];
+      if (k <= i) S[i * R + k] = fma(-S[i * R + j], S[k * R + j], S[i * R + k]);
     }
     __syncthreads();
   }
@@ -260,10 +264,10 @@ __device__ __forceinline__ void system_body(const double* __restrict__ grams, in
     for (int i = c; i < R; ++i) {
       double s = (i == c) ? 1.0 : 0.0;
       for (int k = c; k < i; ++k) {
-        const double xk = (k == c) ? 1.0 / S[c * R + c] : S[c * R + k];
-        s -= S[i * R + k] * xk;
+        const double xk = (k == c) ? __drcp_rn(S[c * R + c]) : S[c * R + k];
+        s = fma(-S[i * R + k], xk, s);
       }
-      const double xi = s / S[i * R + i];
+      const double xi = __ddiv_rn(s, S[i * R + i]);
       if (i > c) S[c * R + i] = xi;
     }
   }
@@ -274,13 +278,14 @@ __device__ __forceinline__ void system_body(const double* __restrict__ grams, in
     const int k0 = r > c ? r : c;
     double acc = 0.0;
     for (int k = k0; k < R; ++k) {
-      const double xr = (k == r) ? 1.0 / S[r * R + r] : S[r * R + k];
-      const double xs = (k == c) ? 1.0 / S[c * R + c] : S[c * R + k];
-      acc += xr * xs;
+      const double xr = (k == r) ? __drcp_rn(S[r * R + r]) : S[r * R + k];
+      const double xs = (k == c) ? __drcp_rn(S[c * R + c]) : S[c * R + k];
+      acc = fma(xr, xs, acc);
     }
     const float hi = (float)acc;
     winv[e] = hi;
-    winv[RR + e] = (float)(acc - (double)hi);
+    winv[RR + e] = (float)__dsub_rn(acc, (double)hi);
+    V[e] = acc;
   }
 }
 
@@ -363,7 +368,7 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ M,
       for (int j = 0; j < RPL; ++j) {
         const int r = rl + LPR * j;
         if (r < R) {
-          const float z = acc[q][j].hi + acc[q][j].lo;
+          const float z = __fadd_rn(acc[q][j].hi, acc[q][j].lo);
           Z[row * R + r] = z;
           df_add_prod(sq[j], z, z);
         }
@@ -456,14 +461,14 @@ __device__ __forceinline__ void fit_body(const double* __restrict__ grams, int N
   if (!bad) {
     for (int e = threadIdx.x; e < RR; e += blockDim.x) {
       double h = 1.0;
-      for (int w = 0; w < N; ++w) h *= grams[(int64_t)w * RR + e];
-      xh += lambda[e / R] * lambda[e % R] * h;
+      for (int w = 0; w < N; ++w) h = __dmul_rn(h, grams[(int64_t)w * RR + e]);
+      xh = fma(__dmul_rn(lambda[e / R], lambda[e % R]), h, xh);
     }
     if (nblocks <= ALS_SERIAL_PARTIALS) {
       for (int r = threadIdx.x; r < R; r += blockDim.x) {
         double v = 0.0;
         for (int b = 0; b < nblocks; ++b) v += inner_part[(int64_t)b * R + r];
-        inn += lambda[r] * v;
+        inn = fma(lambda[r], v, inn);
         lambda_out[r] = lambda[r];
       }
     } else {
@@ -471,7 +476,7 @@ __device__ __forceinline__ void fit_body(const double* __restrict__ grams, int N
       for (int r = warp; r < R; r += nw) {
         const double v = warp_sum_strided(inner_part + r, nblocks, R, lane);
         if (lane == 0) {
-          inn += lambda[r] * v;
+          inn = fma(lambda[r], v, inn);
           lambda_out[r] = lambda[r];
         }
       }
@@ -489,7 +494,7 @@ __device__ __forceinline__ void fit_body(const double* __restrict__ grams, int N
   }
   if (threadIdx.x == 0 && fit && !bad) {
     const double nx = *normX2;
-    double res = nx + red[0] - 2.0 * red2[0];
+    double res = fma(-2.0, red2[0], __dadd_rn(nx, red[0]));
     if (res < 0.0) res = 0.0;
     *fit = nx > 0.0 ? 1.0 - sqrt(res) / sqrt(nx) : 1.0;
   }

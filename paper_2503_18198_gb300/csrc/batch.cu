@@ -68,6 +68,36 @@ __global__ void __launch_bounds__(ALS_THREADS)
                       b.nb_solve[mode], b.live[mode]);
 }
 
+template <int R>
+__global__ void __launch_bounds__(TC_THREADS)
+    batch_tc_solve_kernel(const BatchTensor* __restrict__ bt, const int2* __restrict__ it, int mode) {
+  const int2 tv = it[blockIdx.x];
+  const BatchTensor& b = bt[tv.x];
+  if (!b.active) return;
+  tc_solve_body<R>(b.M, b.chol, b.dims[mode], b.Z, b.colsq_part, b.err, tv.y, b.nb_solve[mode],
+                   b.live[mode]);
+}
+
+template <int R>
+spm_status launch_batch_tc_solve_r(const BatchTensor* bt, const int2* it, int n, int mode,
+                                   cudaStream_t s) {
+  constexpr int smem = (int)TcSolveShape<R>::SMEM;
+  SPM_CUDA_TRY(cudaFuncSetAttribute(batch_tc_solve_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  batch_tc_solve_kernel<R><<<n, TC_THREADS, smem, s>>>(bt, it, mode);
+  SPM_CUDA_TRY(cudaGetLastError());
+  return SPM_OK;
+}
+
+spm_status launch_batch_tc_solve(int R, const BatchTensor* bt, const int2* it, int n, int mode,
+                                 cudaStream_t s) {
+  switch (R) {
+    case 16: return launch_batch_tc_solve_r<16>(bt, it, n, mode, s);
+    case 32: return launch_batch_tc_solve_r<32>(bt, it, n, mode, s);
+    case 64: return launch_batch_tc_solve_r<64>(bt, it, n, mode, s);
+    default: return SPM_ERR_UNSUPPORTED;
+  }
+}
+
 __global__ void batch_lambda_kernel(const BatchTensor* __restrict__ bt, const int2* __restrict__ it,
                                     int mode) {
   const BatchTensor& b = bt[it[blockIdx.x].x];
@@ -295,7 +325,13 @@ spm_status batch_commit(spm_batch_s* B, cudaStream_t s) {
       *cnt = (int)v.size() - *off;
     };
     per_tensor(&I.tens_off, &I.n_tens, [&](int) { return 1; });
-    per_tensor(&I.solve_off, &I.n_solve, [&](int t) { return B->host[t].nb_solve[d]; });
+    per_tensor(&I.solve_off, &I.n_solve, [&](int t) {
+      return tc_solve_rank(B->plans[t]->R) ? 0 : B->host[t].nb_solve[d];
+    });
+    for (int k = 0; k < 3; ++k)
+      per_tensor(&I.tcs_off[k], &I.n_tcs[k], [&](int t) {
+        return B->plans[t]->R == (16 << k) ? B->host[t].nb_solve[d] : 0;
+      });
     per_tensor(&I.scale_off, &I.n_scale, [&](int t) { return B->host[t].nb_scale[d]; });
     per_tensor(&I.gram_off, &I.n_gram, [&](int t) { return B->host[t].nb_gram[d]; });
     per_tensor(&I.fit_off, &I.n_fit, [&](int t) { return d == B->plans[t]->N - 1 ? 1 : 0; });
@@ -356,7 +392,9 @@ spm_status batch_sweep(spm_batch_s* B, cudaStream_t s) {
     const spm_batch_s::ModeItems& I = B->mi[d];
     SPM_TRY(batch_mttkrp(B, d, s));
     batch_system_kernel<<<I.n_tens, ALS_THREADS, 0, s>>>(B->bt, it + I.tens_off, d);
-    batch_solve_kernel<<<I.n_solve, ALS_THREADS, 0, s>>>(B->bt, it + I.solve_off, d);
+    if (I.n_solve > 0) batch_solve_kernel<<<I.n_solve, ALS_THREADS, 0, s>>>(B->bt, it + I.solve_off, d);
+    for (int k = 0; k < 3; ++k)
+      if (I.n_tcs[k] > 0) SPM_TRY(launch_batch_tc_solve(16 << k, B->bt, it + I.tcs_off[k], I.n_tcs[k], d, s));
     batch_lambda_kernel<<<I.n_tens, 256, 0, s>>>(B->bt, it + I.tens_off, d);
     if (B->bf16 == 1)
       batch_scale_kernel<__nv_bfloat16><<<I.n_scale, ALS_THREADS, 0, s>>>(B->bt, it + I.scale_off, d);

@@ -19,7 +19,8 @@ struct spm_batch_s {
     int n_mtt[spm::KC_NONE] = {};  // (tensor, partition) per (N, R) class
     int zero_off = 0, n_zero = 0;  // (tensor, element chunk)
     int tens_off = 0, n_tens = 0;  // (tensor, 0): tensors that have this mode
-    int solve_off = 0, n_solve = 0;  // (tensor, virtual block)
+    int solve_off = 0, n_solve = 0;  // (tensor, virtual block), CUDA-core solve ranks
+    int tcs_off[3] = {}, n_tcs[3] = {};  // the same for the tensor-core solve, R = 16, 32, 64
     int scale_off = 0, n_scale = 0;
     int gram_off = 0, n_gram = 0;
     int fit_off = 0, n_fit = 0;  // tensors whose last mode is this one

@@ -15,7 +15,7 @@
 // be replayed without host round trips.
 #pragma once
 
-#include "als_kernels.cuh"
+#include "als_tc.cuh"
 #include "mttkrp_kernel.cuh"
 
 namespace spm {
