@@ -36,8 +36,13 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int nblocks,
 
 __global__ void __launch_bounds__(ALS_THREADS)
     system_kernel(const double* __restrict__ grams, int N, int d, int R,
-                  double* __restrict__ V, float* __restrict__ winv, int* __restrict__ err) {
+                  double* __restrict__ V, float* __restrict__ winv,
+                  unsigned char* __restrict__ wdig, int* __restrict__ err) {
   system_body(grams, N, d, R, V, winv, err);
+  if (wdig) {
+    __syncthreads();
+    if (!*(volatile int*)err) wdigits_body(V, R, wdig);
+  }
 }
 
 template <int RPL, int LPR>
@@ -50,10 +55,11 @@ __global__ void __launch_bounds__(ALS_THREADS)
 
 template <int R>
 __global__ void __launch_bounds__(TC_THREADS)
-    tc_solve_kernel(const float* __restrict__ M, const double* __restrict__ W, int64_t I,
+    tc_solve_kernel(const float* __restrict__ M, const unsigned char* __restrict__ wdig, int64_t I,
                     float* __restrict__ Z, double* __restrict__ colsq_part,
-                    const int* __restrict__ err, int nvb, const uint32_t* __restrict__ mask) {
-  tc_solve_body<R>(M, W, I, Z, colsq_part, err, blockIdx.x, nvb, mask);
+                    float* __restrict__ colmax_part, const int* __restrict__ err, int nvb,
+                    const uint32_t* __restrict__ mask) {
+  tc_solve_body<R>(M, wdig, I, Z, colsq_part, colmax_part, err, blockIdx.x, nvb, mask);
 }
 
 __global__ void lambda_kernel(const double* __restrict__ colsq_part, int nblocks, int R,
@@ -106,25 +112,14 @@ spm_status launch_gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, 
 
 // The tensor-core row solve over `nb` virtual blocks (R = 16, 32 or 64).
 template <int R>
-spm_status launch_tc_solve_r(int nb, const float* M, const double* W, int64_t I, float* Z,
-                             double* colsq_part, const int* err, const uint32_t* mask,
-                             cudaStream_t s) {
+spm_status launch_tc_solve_r(int nb, const float* M, const unsigned char* wdig, int64_t I, float* Z,
+                             double* colsq_part, float* colmax_part, const int* err,
+                             const uint32_t* mask, cudaStream_t s) {
   constexpr int smem = (int)TcSolveShape<R>::SMEM;
   SPM_CUDA_TRY(cudaFuncSetAttribute(tc_solve_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  tc_solve_kernel<R><<<nb, TC_THREADS, smem, s>>>(M, W, I, Z, colsq_part, err, nb, mask);
+  tc_solve_kernel<R><<<nb, TC_THREADS, smem, s>>>(M, wdig, I, Z, colsq_part, colmax_part, err, nb, mask);
   SPM_CUDA_TRY(cudaGetLastError());
   return SPM_OK;
-}
-
-spm_status launch_tc_solve(int R, int nb, const float* M, const double* W, int64_t I, float* Z,
-                           double* colsq_part, const int* err, const uint32_t* mask,
-                           cudaStream_t s) {
-  switch (R) {
-    case 16: return launch_tc_solve_r<16>(nb, M, W, I, Z, colsq_part, err, mask, s);
-    case 32: return launch_tc_solve_r<32>(nb, M, W, I, Z, colsq_part, err, mask, s);
-    case 64: return launch_tc_solve_r<64>(nb, M, W, I, Z, colsq_part, err, mask, s);
-    default: return SPM_ERR_UNSUPPORTED;
-  }
 }
 
 // The row solve of one mode: tensor cores for R = 16, 32 and 64, else the
@@ -132,16 +127,20 @@ spm_status launch_tc_solve(int R, int nb, const float* M, const double* W, int64
 // inlined into the sweep loop, the equivalent if-chain launched the next
 // variant's instantiation on the aarch64 host build (gcc 13.3, -O2), which
 // the bitwise batch-versus-single sweep test exposed.
-__attribute__((noinline)) spm_status launch_solve(int R, int nb, const float* M, const float* winv,
-                                                  const double* W, int64_t I, float* Z,
-                                                  double* colsq_part, const int* err,
-                                                  const uint32_t* mask, cudaStream_t s) {
-  if (tc_solve_rank(R)) return launch_tc_solve(R, nb, M, W, I, Z, colsq_part, err, mask, s);
+__attribute__((noinline)) spm_status launch_solve(int R, int nb, const spm_als_state& A, int64_t I,
+                                                  const int* err, const uint32_t* mask,
+                                                  cudaStream_t s) {
+  switch (tc_solve_rank(R) ? R : 0) {
+    case 16: return launch_tc_solve_r<16>(nb, A.M, A.wdig, I, A.Z, A.colsq_part, A.colmax_part, err, mask, s);
+    case 32: return launch_tc_solve_r<32>(nb, A.M, A.wdig, I, A.Z, A.colsq_part, A.colmax_part, err, mask, s);
+    case 64: return launch_tc_solve_r<64>(nb, A.M, A.wdig, I, A.Z, A.colsq_part, A.colmax_part, err, mask, s);
+    default: break;
+  }
   switch (R <= 8 ? 0 : R <= 16 ? 1 : R <= 32 ? 2 : 3) {
-    case 0: solve_kernel<1, 8><<<nb, ALS_THREADS, 0, s>>>(M, winv, I, R, Z, colsq_part, err, mask); break;
-    case 1: solve_kernel<1, 16><<<nb, ALS_THREADS, 0, s>>>(M, winv, I, R, Z, colsq_part, err, mask); break;
-    case 2: solve_kernel<1, 32><<<nb, ALS_THREADS, 0, s>>>(M, winv, I, R, Z, colsq_part, err, mask); break;
-    default: solve_kernel<2, 32><<<nb, ALS_THREADS, 0, s>>>(M, winv, I, R, Z, colsq_part, err, mask); break;
+    case 0: solve_kernel<1, 8><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, err, mask); break;
+    case 1: solve_kernel<1, 16><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, err, mask); break;
+    case 2: solve_kernel<1, 32><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, err, mask); break;
+    default: solve_kernel<2, 32><<<nb, ALS_THREADS, 0, s>>>(A.M, A.winv, I, R, A.Z, A.colsq_part, err, mask); break;
   }
   SPM_CUDA_TRY(cudaGetLastError());
   return SPM_OK;
@@ -166,6 +165,8 @@ spm_status ensure_als_state(spmttkrp_plan_s* p) {
   SPM_TRY(plan_alloc(p, (void**)&A.chol, sizeof(double) * RR));
   SPM_TRY(plan_alloc(p, (void**)&A.winv, sizeof(float) * 2 * RR));
   SPM_TRY(plan_alloc(p, (void**)&A.colsq_part, sizeof(double) * R * A.gram_blocks));
+  SPM_TRY(plan_alloc(p, (void**)&A.colmax_part, sizeof(float) * R * A.gram_blocks));
+  if (als_wdig_bytes(R)) SPM_TRY(plan_alloc(p, (void**)&A.wdig, als_wdig_bytes(R)));
   SPM_TRY(plan_alloc(p, (void**)&A.inner_part, sizeof(double) * R * A.gram_blocks));
   SPM_TRY(plan_alloc(p, (void**)&A.lambda_ws, sizeof(double) * R));
   SPM_TRY(plan_alloc(p, (void**)&A.Z, sizeof(float) * (size_t)Imax * R));
@@ -195,11 +196,11 @@ spm_status als_sweep(spmttkrp_plan_s* p, void* const* factors, double* lambda, d
   for (int d = 0; d < N; ++d) {
     const int64_t I = p->dims[d];
     SPM_TRY(run_mttkrp(p, d, factors, A.M, s));
-    system_kernel<<<1, ALS_THREADS, 0, s>>>(A.gram, N, d, R, A.chol, A.winv, p->dev_err);
+    system_kernel<<<1, ALS_THREADS, 0, s>>>(A.gram, N, d, R, A.chol, A.winv, A.wdig, p->dev_err);
     const int nb = als_row_blocks(I, nb_solve);
     // rows without nonzeros in mode d have a zero update: passes skip them
     const uint32_t* live = p->mode[d].empty_rows > 0 ? p->mode[d].rowmask : nullptr;
-    SPM_TRY(launch_solve(R, nb, A.M, A.winv, A.chol, I, A.Z, A.colsq_part, p->dev_err, live, s));
+    SPM_TRY(launch_solve(R, nb, A, I, p->dev_err, live, s));
     lambda_kernel<<<1, 256, 0, s>>>(A.colsq_part, nb, R, A.lambda_ws, p->dev_err);
     const bool last = d == N - 1;
     const int nbs = als_row_blocks(I, nb_solve);

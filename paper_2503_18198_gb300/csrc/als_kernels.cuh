@@ -257,6 +257,9 @@ __device__ __forceinline__ void system_body(const double* __restrict__ grams, in
     if (threadIdx.x == 0) atomicOr(err, DEV_ERR_NUMERIC);
     return;
   }
+  __shared__ double dinv[64];  // 1 / L[c][c], once per column
+  for (int c = threadIdx.x; c < R; c += blockDim.x) dinv[c] = __drcp_rn(S[c * R + c]);
+  __syncthreads();
   // X = L^{-1}, column c by thread c (forward substitution L x = e_c, x_i = 0
   // for i < c), stored transposed in the strictly upper triangle of S:
   // X[i][c] at S[c * R + i] for i > c; X[c][c] = 1 / L[c][c] is recomputed.
@@ -264,7 +267,7 @@ __device__ __forceinline__ void system_body(const double* __restrict__ grams, in
     for (int i = c; i < R; ++i) {
       double s = (i == c) ? 1.0 : 0.0;
       for (int k = c; k < i; ++k) {
-        const double xk = (k == c) ? __drcp_rn(S[c * R + c]) : S[c * R + k];
+        const double xk = (k == c) ? dinv[c] : S[c * R + k];
         s = fma(-S[i * R + k], xk, s);
       }
       const double xi = __ddiv_rn(s, S[i * R + i]);
@@ -278,8 +281,8 @@ __device__ __forceinline__ void system_body(const double* __restrict__ grams, in
     const int k0 = r > c ? r : c;
     double acc = 0.0;
     for (int k = k0; k < R; ++k) {
-      const double xr = (k == r) ? __drcp_rn(S[r * R + r]) : S[r * R + k];
-      const double xs = (k == c) ? __drcp_rn(S[c * R + c]) : S[c * R + k];
+      const double xr = (k == r) ? dinv[r] : S[r * R + k];
+      const double xs = (k == c) ? dinv[c] : S[c * R + k];
       acc = fma(xr, xs, acc);
     }
     const float hi = (float)acc;

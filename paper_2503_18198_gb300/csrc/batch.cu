@@ -47,6 +47,10 @@ __global__ void __launch_bounds__(ALS_THREADS)
   const BatchTensor& b = bt[it[blockIdx.x].x];
   if (!b.active) return;
   system_body(b.gram, b.N, mode, b.R, b.chol, b.winv, b.err);
+  if (b.wdig) {
+    __syncthreads();
+    if (!*(volatile int*)b.err) wdigits_body(b.chol, b.R, b.wdig);
+  }
 }
 
 __global__ void __launch_bounds__(ALS_THREADS)
@@ -74,8 +78,8 @@ __global__ void __launch_bounds__(TC_THREADS)
   const int2 tv = it[blockIdx.x];
   const BatchTensor& b = bt[tv.x];
   if (!b.active) return;
-  tc_solve_body<R>(b.M, b.chol, b.dims[mode], b.Z, b.colsq_part, b.err, tv.y, b.nb_solve[mode],
-                   b.live[mode]);
+  tc_solve_body<R>(b.M, b.wdig, b.dims[mode], b.Z, b.colsq_part, b.colmax_part, b.err, tv.y,
+                   b.nb_solve[mode], b.live[mode]);
 }
 
 template <int R>
@@ -210,6 +214,8 @@ spm_status batch_add(spm_batch_s* B, spmttkrp_plan_s* p, void* const* factors, d
   b.chol = A.chol;
   b.winv = A.winv;
   b.colsq_part = A.colsq_part;
+  b.colmax_part = A.colmax_part;
+  b.wdig = A.wdig;
   b.inner_part = A.inner_part;
   b.lambda_ws = A.lambda_ws;
   b.M = A.M;

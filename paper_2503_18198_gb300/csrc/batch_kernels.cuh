@@ -37,6 +37,8 @@ struct BatchTensor {
   double* chol;
   float* winv;
   double* colsq_part;
+  float* colmax_part;
+  unsigned char* wdig;  // W digit tiles (tensor-core solve ranks), else null
   double* inner_part;
   double* lambda_ws;
   float* M;

@@ -30,6 +30,13 @@ struct spm_mode_copy {
   int scheme = 0;            // 0 cost-balanced, 1 or 2 (Sec. III-B)
 };
 
+// Bytes of the W digit tiles of the tensor-core row solve for rank R: the
+// BF16 digit stack (7 digits x R x R) and R column exponents; ranks 16, 32
+// and 64 only.
+inline constexpr size_t als_wdig_bytes(int R) {
+  return (R == 16 || R == 32 || R == 64) ? (size_t)7 * 2 * R * R + 4 * (size_t)R : 0;
+}
+
 struct spm_als_state {
   bool ready = false;                 // Gram cache valid for `fac_ptr`
   const void* fac_ptr[SPM_MAX_MODES] = {};
@@ -39,6 +46,8 @@ struct spm_als_state {
   double* chol = nullptr;             // R*R: Cholesky factor of V (lower)
   float* winv = nullptr;              // 2*R*R: V^{-1} as hi/lo float pairs
   double* colsq_part = nullptr;       // [gram_blocks][R] column sums of Z^2
+  float* colmax_part = nullptr;       // [gram_blocks][R] column maxima of |Z|
+  unsigned char* wdig = nullptr;      // W = V^{-1} as BF16 digit tiles (tensor-core solve)
   double* inner_part = nullptr;       // [gram_blocks][R] sums of M .* Y
   double* lambda_ws = nullptr;        // R
   float* M = nullptr;                 // Imax*R MTTKRP output
