@@ -53,12 +53,17 @@ def parse():
                     help="skip the batching comparison that the headline line carries")
     ap.add_argument("--workload", default="scale",
                     choices=["scale", "batching", "serving", "precision", "five", "schemes",
-                             "lean", "fibre"],
+                             "lean", "fibre", "probe"],
                     help="scale (default, the headline line); the others print their "
                          "own JSON line")
     ap.add_argument("--tensors", type=int, default=512, help="batching: tensor count")
     ap.add_argument("--sweeps", type=int, default=20, help="batching/precision: ALS sweeps")
     ap.add_argument("--requests", type=int, default=200, help="serving: request count")
+    ap.add_argument("--preset", default="scale", choices=["scale", "precision", "five"],
+                    help="probe: the synthetic preset")
+    ap.add_argument("--factor", default="fp32", choices=["fp32", "bf16"],
+                    help="probe: factor storage type")
+    ap.add_argument("--probe-sweeps", type=int, default=0, help="probe: CP-ALS sweeps")
     return ap.parse_args()
 
 
@@ -395,7 +400,8 @@ def main():
         if rank == 0:  # the extra workloads run on one GPU
             {"batching": run_batching, "serving": run_serving, "precision": run_precision,
              "five": run_precision, "schemes": run_schemes,
-             "lean": run_lean, "fibre": run_fibre}[args.workload](args, rank, world)
+             "lean": run_lean, "fibre": run_fibre,
+             "probe": run_probe}[args.workload](args, rank, world)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
@@ -624,6 +630,49 @@ def run_lean(args, rank, world):
     print(json.dumps({"workload": "lean", "metric": "plan bytes and spMTTKRP ms, full vs lean",
                       "unit": "ms", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
                       "results": out}), flush=True)
+
+
+def run_probe(args, rank, world):
+    """A fixed launch sequence for profiler captures: one plan of --preset at
+    --nnz nonzeros with --factor storage, three warm-up spMTTKRP launches per
+    mode, then one launch per mode (timed by CUDA events and printed), then
+    --probe-sweeps CP-ALS sweeps (each timed).  Profilers select launches with
+    -k / -s / -c on this order; the printed times are not bench values."""
+    import torch
+    import synth
+    import paper_2503_18198_gb300 as spm
+    dims, idx, vals, R, Y = synth.preset_torch(args.preset, nnz=args.nnz, device="cuda")
+    N = len(dims)
+    bf16 = args.factor == "bf16"
+    plan = spm.spmttkrp_plan(dims, idx, vals, R,
+                             spm.SPM_FACTOR_BF16 if bf16 else spm.SPM_FACTOR_FP32)
+    fac = [y.to(torch.bfloat16 if bf16 else torch.float32).clone() for y in Y]
+    outs = [torch.empty(d, R, device="cuda") for d in dims]
+    for _ in range(3):
+        for d in range(N):
+            spm.spmttkrp_run(plan, d, fac, outs[d])
+    torch.cuda.synchronize()
+    ms = []
+    for d in range(N):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        spm.spmttkrp_run(plan, d, fac, outs[d])
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(round(e0.elapsed_time(e1), 4))
+    lam = torch.empty(R, dtype=torch.float64, device="cuda")
+    fit = torch.empty(1, dtype=torch.float64, device="cuda")
+    sweep_ms = []
+    for _ in range(args.probe_sweeps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        spm.cpd_als_step(plan, fac, lam, fit)
+        e1.record()
+        torch.cuda.synchronize()
+        sweep_ms.append(round(e0.elapsed_time(e1), 4))
+    print(json.dumps({"workload": "probe", "preset": args.preset, "factor": args.factor,
+                      "dims": list(dims), "nnz": int(vals.numel()), "rank": R,
+                      "mttkrp_ms_per_mode": ms, "als_sweep_ms": sweep_ms}))
 
 
 def fibre_bytes(dims, nnz, R, distinct, nfib, s_f=4):

@@ -34,15 +34,11 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int nblocks,
   gram_reduce_body(part, nblocks, R, G, err, blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(ALS_THREADS)
+__global__ void __launch_bounds__(SYS_THREADS)
     system_kernel(const double* __restrict__ grams, int N, int d, int R,
                   double* __restrict__ V, float* __restrict__ winv,
                   unsigned char* __restrict__ wdig, int* __restrict__ err) {
-  system_body(grams, N, d, R, V, winv, err);
-  if (wdig) {
-    __syncthreads();
-    if (!*(volatile int*)err) wdigits_body(V, R, wdig);
-  }
+  system_col_body(grams, N, d, R, blockIdx.x, blockIdx.x + 1, V, winv, wdig, err);
 }
 
 template <int RPL, int LPR>
@@ -62,9 +58,20 @@ __global__ void __launch_bounds__(TC_THREADS)
   tc_solve_body<R>(M, wdig, I, Z, colsq_part, colmax_part, err, blockIdx.x, nvb, mask);
 }
 
-__global__ void lambda_kernel(const double* __restrict__ colsq_part, int nblocks, int R,
+__global__ void lambda_kernel(const double* __restrict__ colsq_part,
+                              const float* __restrict__ colmax_part, int nblocks, int R,
                               double* __restrict__ lambda, const int* __restrict__ err) {
-  lambda_body(colsq_part, nblocks, R, lambda, err);
+  lambda_body(colsq_part, colmax_part, nblocks, R, lambda, err, blockIdx.x);
+}
+
+template <typename FT, int R>
+__global__ void __launch_bounds__(TC_THREADS)
+    tc_scale_gram_kernel(const float* __restrict__ Z, const double* __restrict__ lam, int64_t I,
+                         FT* __restrict__ Y, const float* __restrict__ M,
+                         double* __restrict__ gram_part, double* __restrict__ inner_part,
+                         const int* __restrict__ err, const uint32_t* __restrict__ mask) {
+  tc_scale_gram_body<FT, R>(Z, lam, I, Y, M, gram_part, inner_part, err, blockIdx.x, gridDim.x,
+                            mask);
 }
 
 template <typename FT>
@@ -146,6 +153,33 @@ __attribute__((noinline)) spm_status launch_solve(int R, int nb, const spm_als_s
   return SPM_OK;
 }
 
+template <typename FT, int R>
+spm_status launch_tc_scale_gram_r(int nb, const spm_als_state& A, int64_t I, void* Y, bool last,
+                                  const int* err, const uint32_t* mask, cudaStream_t s) {
+  constexpr int smem = (int)TcGramShape<R>::SMEM;
+  SPM_CUDA_TRY(cudaFuncSetAttribute(tc_scale_gram_kernel<FT, R>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  tc_scale_gram_kernel<FT, R><<<nb, TC_THREADS, smem, s>>>(A.Z, A.lambda_ws, I, static_cast<FT*>(Y),
+                                                          last ? A.M : nullptr, A.gram_part,
+                                                          A.inner_part, err, mask);
+  SPM_CUDA_TRY(cudaGetLastError());
+  return SPM_OK;
+}
+
+// Y = Z / lambda and the Gram partials of the stored Y (and the inner-product
+// partials on the last mode) in one tensor-core pass (R = 16, 32).
+__attribute__((noinline)) spm_status launch_tc_scale_gram(int R, bool bf16, int nb,
+                                                          const spm_als_state& A, int64_t I,
+                                                          void* Y, bool last, const int* err,
+                                                          const uint32_t* mask, cudaStream_t s) {
+  switch ((R == 32 ? 1 : 0) + (bf16 ? 2 : 0)) {
+    case 0: return launch_tc_scale_gram_r<float, 16>(nb, A, I, Y, last, err, mask, s);
+    case 1: return launch_tc_scale_gram_r<float, 32>(nb, A, I, Y, last, err, mask, s);
+    case 2: return launch_tc_scale_gram_r<__nv_bfloat16, 16>(nb, A, I, Y, last, err, mask, s);
+    default: return launch_tc_scale_gram_r<__nv_bfloat16, 32>(nb, A, I, Y, last, err, mask, s);
+  }
+}
+
 spm_status gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, cudaStream_t s,
                 const uint32_t* mask) {
   return p->bf16 ? launch_gram<__nv_bfloat16>(p, Y, I, G, s, mask)
@@ -168,7 +202,7 @@ spm_status ensure_als_state(spmttkrp_plan_s* p) {
   SPM_TRY(plan_alloc(p, (void**)&A.colmax_part, sizeof(float) * R * A.gram_blocks));
   if (als_wdig_bytes(R)) SPM_TRY(plan_alloc(p, (void**)&A.wdig, als_wdig_bytes(R)));
   SPM_TRY(plan_alloc(p, (void**)&A.inner_part, sizeof(double) * R * A.gram_blocks));
-  SPM_TRY(plan_alloc(p, (void**)&A.lambda_ws, sizeof(double) * R));
+  SPM_TRY(plan_alloc(p, (void**)&A.lambda_ws, sizeof(double) * 2 * R));  // lambda, Gram scales
   SPM_TRY(plan_alloc(p, (void**)&A.Z, sizeof(float) * (size_t)Imax * R));
   SPM_TRY(plan_alloc(p, (void**)&A.M, sizeof(float) * (size_t)Imax * R));
   return SPM_OK;
@@ -196,27 +230,37 @@ spm_status als_sweep(spmttkrp_plan_s* p, void* const* factors, double* lambda, d
   for (int d = 0; d < N; ++d) {
     const int64_t I = p->dims[d];
     SPM_TRY(run_mttkrp(p, d, factors, A.M, s));
-    system_kernel<<<1, ALS_THREADS, 0, s>>>(A.gram, N, d, R, A.chol, A.winv, A.wdig, p->dev_err);
+    system_kernel<<<R, SYS_THREADS, 0, s>>>(A.gram, N, d, R, A.chol, A.winv, A.wdig, p->dev_err);
     const int nb = als_row_blocks(I, nb_solve);
     // rows without nonzeros in mode d have a zero update: passes skip them
     const uint32_t* live = p->mode[d].empty_rows > 0 ? p->mode[d].rowmask : nullptr;
     SPM_TRY(launch_solve(R, nb, A, I, p->dev_err, live, s));
-    lambda_kernel<<<1, 256, 0, s>>>(A.colsq_part, nb, R, A.lambda_ws, p->dev_err);
+    const bool tcg = tc_gram_rank(R);
+    lambda_kernel<<<R, 32, 0, s>>>(A.colsq_part, tcg ? A.colmax_part : nullptr, nb, R,
+                                    A.lambda_ws, p->dev_err);
     const bool last = d == N - 1;
-    const int nbs = als_row_blocks(I, nb_solve);
-    if (p->bf16)
-      scale_kernel<__nv_bfloat16><<<nbs, ALS_THREADS, 0, s>>>(
-          A.Z, A.lambda_ws, I, R, static_cast<__nv_bfloat16*>(factors[d]), last ? A.M : nullptr,
-          A.inner_part, p->dev_err, live);
-    else
-      scale_kernel<float><<<nbs, ALS_THREADS, 0, s>>>(A.Z, A.lambda_ws, I, R,
-                                                       static_cast<float*>(factors[d]),
-                                                       last ? A.M : nullptr, A.inner_part,
-                                                       p->dev_err, live);
-    SPM_CUDA_TRY(cudaGetLastError());
-    SPM_TRY(gram(p, factors[d], I, A.gram + (size_t)d * R * R, s, live));
+    int nin;  // inner-product partials of the last mode
+    if (tcg) {
+      nin = tc_gram_blocks(I, A.gram_blocks);
+      SPM_TRY(launch_tc_scale_gram(R, p->bf16, nin, A, I, factors[d], last, p->dev_err, live, s));
+      gram_reduce_kernel<<<std::max(1, std::min(1024, R * R / 8)), 256, 0, s>>>(
+          A.gram_part, nin, R, A.gram + (size_t)d * R * R, p->dev_err);
+    } else {
+      nin = als_row_blocks(I, nb_solve);
+      if (p->bf16)
+        scale_kernel<__nv_bfloat16><<<nin, ALS_THREADS, 0, s>>>(
+            A.Z, A.lambda_ws, I, R, static_cast<__nv_bfloat16*>(factors[d]), last ? A.M : nullptr,
+            A.inner_part, p->dev_err, live);
+      else
+        scale_kernel<float><<<nin, ALS_THREADS, 0, s>>>(A.Z, A.lambda_ws, I, R,
+                                                         static_cast<float*>(factors[d]),
+                                                         last ? A.M : nullptr, A.inner_part,
+                                                         p->dev_err, live);
+      SPM_CUDA_TRY(cudaGetLastError());
+      SPM_TRY(gram(p, factors[d], I, A.gram + (size_t)d * R * R, s, live));
+    }
     if (last) {
-      fit_kernel<<<1, ALS_THREADS, 0, s>>>(A.gram, N, R, A.lambda_ws, A.inner_part, nbs,
+      fit_kernel<<<1, ALS_THREADS, 0, s>>>(A.gram, N, R, A.lambda_ws, A.inner_part, nin,
                                            p->normX2, fit, lambda, p->dev_err);
     }
   }

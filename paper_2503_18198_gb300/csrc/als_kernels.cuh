@@ -56,7 +56,17 @@ __device__ __forceinline__ double df_value(const df& a) { return __dadd_rn((doub
 __device__ __forceinline__ double warp_sum_strided(const double* __restrict__ x, int n,
                                                    int64_t stride, int lane) {
   double s = 0.0;
-  for (int b = lane; b < n; b += 32) s += x[(int64_t)b * stride];
+  // loads 8 at a time ahead of the (ordered) additions: the latency of the
+  // strided reads overlaps, the sum is the same
+  int b = lane;
+  for (; b + 7 * 32 < n; b += 8 * 32) {
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = x[(int64_t)(b + 32 * k) * stride];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += v[k];
+  }
+  for (; b < n; b += 32) s += x[(int64_t)b * stride];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(SPM_FULL_MASK, s, o);
   return __shfl_sync(SPM_FULL_MASK, s, 0);
@@ -212,87 +222,6 @@ __device__ __forceinline__ void gram_reduce_body(const double* __restrict__ part
 }
 
 // ---------------------------------------------------------------------------
-// V = Hadamard of the other Grams; Cholesky; W = V^{-1} as FP32 hi/lo pairs.
-// One block.  `chol` (R*R doubles) is the working matrix.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void system_body(const double* __restrict__ grams, int N, int d, int R,
-                                            double* __restrict__ V, float* __restrict__ winv,
-                                            int* __restrict__ err) {
-  // The R x R working matrix lives in shared memory (R <= 64); V^{-1} is
-  // written to `V` in FP64 (the tensor-core solve splits it) and to `winv`
-  // as FP32 hi/lo pairs (the CUDA-core solve).
-  __shared__ double S[64 * 64];
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = *err ? 1 : 0;
-  __syncthreads();
-  if (bad) return;
-  const int RR = R * R;
-  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-    double v = 1.0;
-    for (int w = 0; w < N; ++w)
-      if (w != d) v = __dmul_rn(v, grams[(int64_t)w * RR + e]);
-    S[e] = v;
-  }
-  __syncthreads();
-  // right-looking Cholesky, lower triangle of S becomes L
-  for (int j = 0; j < R; ++j) {
-    if (threadIdx.x == 0) {
-      const double piv = S[j * R + j];
-      if (!(piv > 0.0) || !isfinite(piv)) bad = 1;
-      else S[j * R + j] = sqrt(piv);
-    }
-    __syncthreads();
-    if (bad) break;
-    const double ljj = S[j * R + j];
-    for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) S[i * R + j] = __ddiv_rn(S[i * R + j], ljj);
-    __syncthreads();
-    const int m = R - j - 1;  // trailing (m x m) lower triangle update
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = j + 1 + e / m, k = j + 1 + e % m;
-      if (k <= i) S[i * R + k] = fma(-S[i * R + j], S[k * R + j], S[i * R + k]);
-    }
-    __syncthreads();
-  }
-  if (bad) {
-    if (threadIdx.x == 0) atomicOr(err, DEV_ERR_NUMERIC);
-    return;
-  }
-  __shared__ double dinv[64];  // 1 / L[c][c], once per column
-  for (int c = threadIdx.x; c < R; c += blockDim.x) dinv[c] = __drcp_rn(S[c * R + c]);
-  __syncthreads();
-  // X = L^{-1}, column c by thread c (forward substitution L x = e_c, x_i = 0
-  // for i < c), stored transposed in the strictly upper triangle of S:
-  // X[i][c] at S[c * R + i] for i > c; X[c][c] = 1 / L[c][c] is recomputed.
-  for (int c = threadIdx.x; c < R; c += blockDim.x) {
-    for (int i = c; i < R; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int k = c; k < i; ++k) {
-        const double xk = (k == c) ? dinv[c] : S[c * R + k];
-        s = fma(-S[i * R + k], xk, s);
-      }
-      const double xi = __ddiv_rn(s, S[i * R + i]);
-      if (i > c) S[c * R + i] = xi;
-    }
-  }
-  __syncthreads();
-  // W = X^T X:  W[r][s] = sum_{k >= max(r,s)} X[k][r] X[k][s]
-  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-    const int r = e / R, c = e % R;
-    const int k0 = r > c ? r : c;
-    double acc = 0.0;
-    for (int k = k0; k < R; ++k) {
-      const double xr = (k == r) ? dinv[r] : S[r * R + k];
-      const double xs = (k == c) ? dinv[c] : S[c * R + k];
-      acc = fma(xr, xs, acc);
-    }
-    const float hi = (float)acc;
-    winv[e] = hi;
-    winv[RR + e] = (float)__dsub_rn(acc, (double)hi);
-    V[e] = acc;
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Z = M W (double-float), column sums of Z^2 per block.  LPR lanes hold one
 // row (LPR = 8, 16 or 32 >= R, or 32 with RPL = 2 for R <= 64), so a warp
 // instruction covers 32 / LPR rows and one warp iteration ROWS of those;
@@ -390,22 +319,44 @@ __device__ __forceinline__ void solve_body(const float* __restrict__ M,
   }
 }
 
-__device__ __forceinline__ void lambda_body(const double* __restrict__ colsq_part, int nblocks,
+// Scale exponent g of a column of the new factor for the tensor-core Gram:
+// |Y(i, r)| < 2^(g - 1) for Y = Z / lambda rounded to FP32 or BF16, from the
+// column's max |Z| (0 for a zero column).
+__device__ __forceinline__ int gram_scale_exp(float cmax, double lam) {
+  const float inv = lam > 0.0 ? (float)(1.0 / lam) : 1.f;
+  const double b = (double)cmax * (double)inv * (1.0 + 1.0 / 128.0);
+  if (!(b > 0.0)) return 0;
+  int e;
+  (void)frexp(b, &e);  // b < 2^e
+  return e + 1;
+}
+
+// lambda(r) = sqrt(sum of the column-r partials of Z^2) and, when
+// colmax_part is non-null, lambda(R + r) = the Gram scale exponent of column r
+// -- one warp per column (FP64 work spread over blocks: the FP64 pipe of one
+// SM would serialise a whole mode's columns).
+__device__ __forceinline__ void lambda_body(const double* __restrict__ colsq_part,
+                                            const float* __restrict__ colmax_part, int nblocks,
                                             int R, double* __restrict__ lambda,
-                                            const int* __restrict__ err) {
-  if (warp_err(err)) return;
+                                            const int* __restrict__ err, int r) {
+  if (warp_err(err) || r >= R) return;
+  const int lane = threadIdx.x & 31;
+  double v;
   if (nblocks <= ALS_SERIAL_PARTIALS) {
-    for (int r = threadIdx.x; r < R; r += blockDim.x) {
-      double v = 0.0;
+    v = 0.0;
+    if (lane == 0)
       for (int b = 0; b < nblocks; ++b) v += colsq_part[(int64_t)b * R + r];
-      lambda[r] = sqrt(v);
-    }
-    return;
+  } else {
+    v = warp_sum_strided(colsq_part + r, nblocks, R, lane);
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = warp; r < R; r += nw) {
-    const double v = warp_sum_strided(colsq_part + r, nblocks, R, lane);
-    if (lane == 0) lambda[r] = sqrt(v);
+  int mb = 0;  // max |Z| as the bits of a non-negative float
+  if (colmax_part) {
+    for (int b = lane; b < nblocks; b += 32) mb = max(mb, __float_as_int(colmax_part[(int64_t)b * R + r]));
+    mb = __reduce_max_sync(SPM_FULL_MASK, mb);
+  }
+  if (lane == 0) {
+    lambda[r] = sqrt(v);
+    if (colmax_part) lambda[R + r] = (double)gram_scale_exp(__int_as_float(mb), lambda[r]);
   }
 }
 

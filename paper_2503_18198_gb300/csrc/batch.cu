@@ -42,15 +42,12 @@ __global__ void batch_fixup_kernel(const BatchTensor* __restrict__ bt, const int
   mttkrp_fixup_body(a.cta_part, a.cta_meta, b.kappa, b.R, b.M, tz.y, threadIdx.x & 31);
 }
 
-__global__ void __launch_bounds__(ALS_THREADS)
+// One block per tensor: its system factored once, its columns by the warps.
+__global__ void __launch_bounds__(SYS_THREADS)
     batch_system_kernel(const BatchTensor* __restrict__ bt, const int2* __restrict__ it, int mode) {
   const BatchTensor& b = bt[it[blockIdx.x].x];
   if (!b.active) return;
-  system_body(b.gram, b.N, mode, b.R, b.chol, b.winv, b.err);
-  if (b.wdig) {
-    __syncthreads();
-    if (!*(volatile int*)b.err) wdigits_body(b.chol, b.R, b.wdig);
-  }
+  system_col_body(b.gram, b.N, mode, b.R, 0, b.R, b.chol, b.winv, b.wdig, b.err);
 }
 
 __global__ void __launch_bounds__(ALS_THREADS)
@@ -102,11 +99,48 @@ spm_status launch_batch_tc_solve(int R, const BatchTensor* bt, const int2* it, i
   }
 }
 
+// Block (x, y): column y of tensor it[x] (one warp).
 __global__ void batch_lambda_kernel(const BatchTensor* __restrict__ bt, const int2* __restrict__ it,
                                     int mode) {
   const BatchTensor& b = bt[it[blockIdx.x].x];
   if (!b.active) return;
-  lambda_body(b.colsq_part, b.nb_solve[mode], b.R, b.lambda_ws, b.err);
+  lambda_body(b.colsq_part, tc_gram_rank(b.R) ? b.colmax_part : nullptr, b.nb_solve[mode], b.R,
+              b.lambda_ws, b.err, blockIdx.y);
+}
+
+// Y = Z / lambda with the Gram and inner-product partials on the tensor cores
+// (R = 16, 32): item (tensor, virtual block).
+template <typename FT, int R>
+__global__ void __launch_bounds__(TC_THREADS)
+    batch_tc_scale_gram_kernel(const BatchTensor* __restrict__ bt, const int2* __restrict__ it,
+                               int mode) {
+  const int2 tv = it[blockIdx.x];
+  const BatchTensor& b = bt[tv.x];
+  if (!b.active) return;
+  tc_scale_gram_body<FT, R>(b.Z, b.lambda_ws, b.dims[mode], static_cast<FT*>(b.fac[mode]),
+                            mode == b.N - 1 ? b.M : nullptr, b.gram_part, b.inner_part, b.err,
+                            tv.y, b.nb_scale[mode], b.live[mode]);
+}
+
+template <typename FT, int R>
+spm_status launch_batch_tc_scale_gram_r(const BatchTensor* bt, const int2* it, int n, int mode,
+                                        cudaStream_t s) {
+  constexpr int smem = (int)TcGramShape<R>::SMEM;
+  SPM_CUDA_TRY(cudaFuncSetAttribute(batch_tc_scale_gram_kernel<FT, R>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  batch_tc_scale_gram_kernel<FT, R><<<n, TC_THREADS, smem, s>>>(bt, it, mode);
+  SPM_CUDA_TRY(cudaGetLastError());
+  return SPM_OK;
+}
+
+spm_status launch_batch_tc_scale_gram(int R, bool bf16, const BatchTensor* bt, const int2* it,
+                                      int n, int mode, cudaStream_t s) {
+  switch ((R == 32 ? 1 : 0) + (bf16 ? 2 : 0)) {
+    case 0: return launch_batch_tc_scale_gram_r<float, 16>(bt, it, n, mode, s);
+    case 1: return launch_batch_tc_scale_gram_r<float, 32>(bt, it, n, mode, s);
+    case 2: return launch_batch_tc_scale_gram_r<__nv_bfloat16, 16>(bt, it, n, mode, s);
+    default: return launch_batch_tc_scale_gram_r<__nv_bfloat16, 32>(bt, it, n, mode, s);
+  }
 }
 
 template <typename FT>
@@ -256,6 +290,8 @@ spm_status batch_add(spm_batch_s* B, spmttkrp_plan_s* p, void* const* factors, d
     b.gram_rpb[d] = ceil_div<int64_t>(I, b.nb_gram[d]);
     b.nb_solve[d] = als_row_blocks(I, A.gram_blocks);
     b.nb_scale[d] = als_row_blocks(I, A.gram_blocks);
+    if (tc_gram_rank(p->R))  // the tensor-core normalisation/Gram pass: its own split
+      b.nb_gram[d] = b.nb_scale[d] = tc_gram_blocks(I, A.gram_blocks);
   }
   for (int w = 0; w < p->N; ++w)
     SPM_TRY(gram(p, factors[w], p->dims[w], A.gram + (size_t)w * p->R * p->R, s));
@@ -285,10 +321,12 @@ spm_status batch_commit(spm_batch_s* B, cudaStream_t s) {
   if (!B->dirty) return SPM_OK;
   const int n = (int)B->host.size();
   B->maxN = 0;
+  B->maxR = 1;
   for (int kc = 0; kc < KC_NONE; ++kc) B->mtt_smem[kc] = 0;
   for (int t = 0; t < n; ++t) {
     const spmttkrp_plan_s* p = B->plans[t];
     B->maxN = std::max(B->maxN, p->N);
+    B->maxR = std::max(B->maxR, p->R);
     // partitions may have changed since the tensor was added (autotuning)
     B->host[t].kappa = p->kappa;
     for (int d = 0; d < p->N; ++d) B->host[t].margs[d].woff = p->mode[d].woff;
@@ -336,10 +374,20 @@ spm_status batch_commit(spm_batch_s* B, cudaStream_t s) {
     });
     for (int k = 0; k < 3; ++k)
       per_tensor(&I.tcs_off[k], &I.n_tcs[k], [&](int t) {
-        return B->plans[t]->R == (16 << k) ? B->host[t].nb_solve[d] : 0;
+        const int R = B->plans[t]->R;
+        return tc_solve_rank(R) && R == (16 << k) ? B->host[t].nb_solve[d] : 0;
       });
-    per_tensor(&I.scale_off, &I.n_scale, [&](int t) { return B->host[t].nb_scale[d]; });
-    per_tensor(&I.gram_off, &I.n_gram, [&](int t) { return B->host[t].nb_gram[d]; });
+    per_tensor(&I.scale_off, &I.n_scale, [&](int t) {
+      return tc_gram_rank(B->plans[t]->R) ? 0 : B->host[t].nb_scale[d];
+    });
+    per_tensor(&I.gram_off, &I.n_gram, [&](int t) {
+      return tc_gram_rank(B->plans[t]->R) ? 0 : B->host[t].nb_gram[d];
+    });
+    for (int k = 0; k < 2; ++k)
+      per_tensor(&I.tcg_off[k], &I.n_tcg[k], [&](int t) {
+        const int R = B->plans[t]->R;
+        return tc_gram_rank(R) && R == (16 << k) ? B->host[t].nb_scale[d] : 0;
+      });
     per_tensor(&I.fit_off, &I.n_fit, [&](int t) { return d == B->plans[t]->N - 1 ? 1 : 0; });
   }
   SPM_TRY(grow(&B->bt, &B->bt_cap, std::max<size_t>(1, n)));
@@ -397,19 +445,27 @@ spm_status batch_sweep(spm_batch_s* B, cudaStream_t s) {
   for (int d = 0; d < B->maxN; ++d) {
     const spm_batch_s::ModeItems& I = B->mi[d];
     SPM_TRY(batch_mttkrp(B, d, s));
-    batch_system_kernel<<<I.n_tens, ALS_THREADS, 0, s>>>(B->bt, it + I.tens_off, d);
+    batch_system_kernel<<<I.n_tens, SYS_THREADS, 0, s>>>(B->bt, it + I.tens_off, d);
     if (I.n_solve > 0) batch_solve_kernel<<<I.n_solve, ALS_THREADS, 0, s>>>(B->bt, it + I.solve_off, d);
     for (int k = 0; k < 3; ++k)
       if (I.n_tcs[k] > 0) SPM_TRY(launch_batch_tc_solve(16 << k, B->bt, it + I.tcs_off[k], I.n_tcs[k], d, s));
-    batch_lambda_kernel<<<I.n_tens, 256, 0, s>>>(B->bt, it + I.tens_off, d);
-    if (B->bf16 == 1)
-      batch_scale_kernel<__nv_bfloat16><<<I.n_scale, ALS_THREADS, 0, s>>>(B->bt, it + I.scale_off, d);
-    else
-      batch_scale_kernel<float><<<I.n_scale, ALS_THREADS, 0, s>>>(B->bt, it + I.scale_off, d);
-    if (B->bf16 == 1)
-      batch_gram_kernel<__nv_bfloat16><<<I.n_gram, ALS_THREADS, 0, s>>>(B->bt, it + I.gram_off, d);
-    else
-      batch_gram_kernel<float><<<I.n_gram, ALS_THREADS, 0, s>>>(B->bt, it + I.gram_off, d);
+    batch_lambda_kernel<<<dim3(I.n_tens, B->maxR), 32, 0, s>>>(B->bt, it + I.tens_off, d);
+    if (I.n_scale > 0) {
+      if (B->bf16 == 1)
+        batch_scale_kernel<__nv_bfloat16><<<I.n_scale, ALS_THREADS, 0, s>>>(B->bt, it + I.scale_off, d);
+      else
+        batch_scale_kernel<float><<<I.n_scale, ALS_THREADS, 0, s>>>(B->bt, it + I.scale_off, d);
+    }
+    if (I.n_gram > 0) {
+      if (B->bf16 == 1)
+        batch_gram_kernel<__nv_bfloat16><<<I.n_gram, ALS_THREADS, 0, s>>>(B->bt, it + I.gram_off, d);
+      else
+        batch_gram_kernel<float><<<I.n_gram, ALS_THREADS, 0, s>>>(B->bt, it + I.gram_off, d);
+    }
+    for (int k = 0; k < 2; ++k)
+      if (I.n_tcg[k] > 0)
+        SPM_TRY(launch_batch_tc_scale_gram(16 << k, B->bf16 == 1, B->bt, it + I.tcg_off[k],
+                                           I.n_tcg[k], d, s));
     batch_gram_reduce_kernel<<<I.n_tens, 256, 0, s>>>(B->bt, it + I.tens_off, d);
     if (I.n_fit > 0) batch_fit_kernel<<<I.n_fit, ALS_THREADS, 0, s>>>(B->bt, it + I.fit_off, d);
     SPM_CUDA_TRY(cudaGetLastError());

@@ -21,11 +21,13 @@ struct spm_batch_s {
     int tens_off = 0, n_tens = 0;  // (tensor, 0): tensors that have this mode
     int solve_off = 0, n_solve = 0;  // (tensor, virtual block), CUDA-core solve ranks
     int tcs_off[3] = {}, n_tcs[3] = {};  // the same for the tensor-core solve, R = 16, 32, 64
-    int scale_off = 0, n_scale = 0;
-    int gram_off = 0, n_gram = 0;
+    int scale_off = 0, n_scale = 0;  // CUDA-core normalisation (ranks without the tensor-core pass)
+    int tcg_off[2] = {}, n_tcg[2] = {};  // tensor-core normalisation + Gram, R = 16, 32
+    int gram_off = 0, n_gram = 0;    // CUDA-core Gram partials
     int fit_off = 0, n_fit = 0;  // tensors whose last mode is this one
   } mi[SPM_MAX_MODES];
   int maxN = 0;
+  int maxR = 1;  // largest rank of the members (grid of the system launch)
   // device memory of the batch itself
   spm::BatchTensor* bt = nullptr;
   size_t bt_cap = 0;

@@ -867,7 +867,7 @@ void plan_bytes_estimate(int N, const int64_t* dims, int64_t nnz, int R, int kap
     const size_t gb = (size_t)std::max(1, sm_count()) * 4;
     const size_t RR = (size_t)R * R;
     b += sizeof(double) * RR * N + sizeof(double) * RR * gb + sizeof(double) * RR;
-    b += sizeof(float) * 2 * RR + sizeof(double) * R * gb * 2 + sizeof(double) * R;
+    b += sizeof(float) * 2 * RR + sizeof(double) * R * gb * 2 + sizeof(double) * 2 * R;
     b += sizeof(float) * R * gb + als_wdig_bytes(R);  // column maxima of Z, W digit tiles
     b += sizeof(float) * (size_t)Imax * R * 2;
   }
