@@ -462,14 +462,22 @@ def main():
     peak, peak_kind = measured_peak()
     achieved = sum(B) / (sum(mode_ms) * 1e-3) / 1e9
     traffic = None
+    traffic_small = None  # counters of a smaller case of the same kernel, reported beside
     tfile = os.path.join(ROOT, "profiles", "mttkrp_traffic.json")
     if os.path.exists(tfile):
         try:
             with open(tfile) as f:
                 tj = json.load(f)
-            # counters taken on this workload with the current kernel sources only
-            if tj.get("nnz") == nnz and tj.get("kernel_digest") == kernel_digest():
-                traffic = tj.get("bytes_per_launch")
+            # counters taken with the current kernel sources only; `traffic`
+            # only from this workload (they do not scale with the nonzeros)
+            if tj.get("kernel_digest") == kernel_digest():
+                if tj.get("nnz") == nnz:
+                    traffic = tj.get("bytes_per_launch")
+                else:
+                    traffic_small = {"nnz": tj.get("nnz"),
+                                     "bytes_per_launch": tj.get("bytes_per_launch"),
+                                     "over_algorithmic": tj.get("traffic_over_algorithmic"),
+                                     "source": "profiles/mttkrp_traffic.json"}
         except (OSError, ValueError):
             traffic = None
 
@@ -557,6 +565,7 @@ def main():
             "algorithmic_bytes_per_mode": B,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "traffic_smaller_case": traffic_small,
                          "kernel": "mttkrp_kernel (+ row zero-fill and partition fix-up of the same call)",
                          "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
             "cpu_baseline": cpu,
