@@ -93,6 +93,18 @@ __device__ __forceinline__ int scale_expf(float amax) {
   return e;
 }
 
+// rint(y) for abs(y) <= 2^22 by the 1.5 * 2^23 shift (round half to even, like
+// rintf; two adds on the FMA pipe instead of the conversion pipe).
+__device__ __forceinline__ float round_int(float y) {
+  return __fsub_rn(__fadd_rn(y, 12582912.f), 12582912.f);
+}
+
+// Two integer-valued floats of magnitude <= 256 as a BF16 pair (lo = a): their
+// low 16 bits are zero, so the BF16 value is the high half, exactly.
+__device__ __forceinline__ uint32_t pack_bf16_int(float a, float b) {
+  return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+}
+
 __device__ __forceinline__ void df_add(df& a, float x) {  // a += x (error-free two-sum)
   const float s = __fadd_rn(a.hi, x);
   const float bb = __fsub_rn(s, a.hi);
@@ -360,14 +372,12 @@ __device__ __forceinline__ void tc_solve_body(const float* __restrict__ M,
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const float y = __fmul_rn(x[j], 128.f);
-            k[j] = rintf(y);
+            k[j] = round_int(y);
             x[j] = __fsub_rn(y, k[j]);
           }
-          __nv_bfloat162 h[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(k[2 * j], k[2 * j + 1]);
           *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(rl, p * R + half * H + gg * 8, S::KA)) =
-              *reinterpret_cast<uint4*>(h);
+              make_uint4(pack_bf16_int(k[0], k[1]), pack_bf16_int(k[2], k[3]),
+                         pack_bf16_int(k[4], k[5]), pack_bf16_int(k[6], k[7]));
         }
       }
       fence_proxy_async_smem();  // digits visible to the tensor core
@@ -627,14 +637,12 @@ __device__ __forceinline__ void tc_scale_gram_body(const float* __restrict__ Z,
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) {
           const float yy = __fmul_rn(x[jj], 128.f);
-          k[jj] = rintf(yy);
+          k[jj] = round_int(yy);
           x[jj] = __fsub_rn(yy, k[jj]);
         }
-        __nv_bfloat162 h[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(k[2 * q], k[2 * q + 1]);
         *reinterpret_cast<uint4*>(A + tc::kmajor_offset(p * R + r, k0, GT_ROWS)) =
-            *reinterpret_cast<uint4*>(h);
+            make_uint4(pack_bf16_int(k[0], k[1]), pack_bf16_int(k[2], k[3]),
+                       pack_bf16_int(k[4], k[5]), pack_bf16_int(k[6], k[7]));
       }
     }
     fence_proxy_async_smem();  // digits visible to the tensor core
