@@ -525,6 +525,21 @@ spm_status spm_selftest_mttkrp_timeout(spmttkrp_plan_t plan, int mode,
                                        const void *const *factors, float *out,
                                        void *stream);
 
+/* The CP-ALS row passes of one mode on caller data, for precision tests of
+ * the tensor-core arithmetic (Sec. II-A5's update; the splitting is stated in
+ * the library's design notes).  Device pointers: M (I x R FP32, row-major),
+ * V (R x R FP64, symmetric positive definite).  Runs the library's kernels:
+ * W = V^{-1} by the FP64 Cholesky (one block per column) with W's BF16 digit
+ * stack, Z = M W on the tensor cores (Z: I x R FP32), lambda = column 2-norms
+ * of Z (R doubles), Y = Z / lambda (I x R FP32) and, for R = 16 or 32,
+ * G = Y^T Y on the tensor cores from the stored Y (R x R FP64; untouched for
+ * R = 64).  R must be 16, 32 or 64 and I >= 1 (else SPM_ERR_UNSUPPORTED /
+ * SPM_ERR_INVALID_ARG); V not positive definite gives SPM_ERR_NUMERIC.
+ * Allocates and frees its own scratch; synchronises `stream`. */
+spm_status spm_selftest_tc_rowpass(int R, int64_t I, const float *M, const double *V,
+                                   float *Z, float *Y, double *G, double *lambda,
+                                   void *stream);
+
 /* Fault injection on the host: the k-th device allocation made for a plan
  * from now on (k = 0: the next one) fails as if cudaMalloc had run out of
  * memory; k < 0 disables.  One-shot.  For tests of the error paths. */

@@ -12,7 +12,7 @@ from .binding import (SPM_FACTOR_BF16, SPM_FACTOR_FP32, SPM_KAPPA,  # noqa: F401
                       cpd_als_step,
                       load, spm_batch_autotune, spm_batch_create, spm_batch_destroy, spm_batch_status,
                       spm_batch_sweep,
-                      spm_device_sm_count, spm_status_string, spmttkrp_plan,
+                      spm_device_sm_count, spm_selftest_tc_rowpass, spm_status_string, spmttkrp_plan,
                       spmttkrp_plan_bytes, spmttkrp_plan_bytes_estimate,
                       spmttkrp_plan_destroy, spmttkrp_plan_fibre_count,
                       spmttkrp_plan_partition, spmttkrp_plan_permutation,

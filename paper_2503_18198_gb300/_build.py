@@ -19,14 +19,11 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 SO_NAME = "libspmttkrp.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# -fmad=false: no implicit contraction of a multiply and an add into an FMA.
-# Every FMA the kernels rely on is written explicitly (fmaf, fma, packed
-# f32x2 instructions), so this changes no intended arithmetic; it makes the
-# bits of an expression independent of the kernel and translation unit it is
-# compiled into (batched and single-tensor sweeps must agree bitwise).
 # -fno-ipa-icf: no identical-code folding of host functions, so that no two
-# kernel launch stubs (one per template instantiation) are ever merged.
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-fmad=false",
+# kernel launch stubs (one per template instantiation) are ever merged.  (The
+# ALS device bodies shared by the batched and single-tensor sweeps write every
+# rounding explicitly, so their bits do not depend on FMA contraction.)
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-fno-ipa-icf",
               "-I" + os.path.join(ROOT, "include")]
 

@@ -70,7 +70,7 @@ SYMBOLS = ("spmttkrp_plan", "spmttkrp_plan_bytes", "spmttkrp_plan_permutation",
            "spm_server_destroy", "spm_selftest_wait_timeout", "spm_inject_alloc_failure",
            "cpd_als_reset", "spm_server_snapshot", "spm_server_resume",
            "spmttkrp_run_all_host", "spm_selftest_mttkrp_timeout", "spmttkrp_noalloc_status",
-           "spmttkrp_plan_fibre_count")
+           "spmttkrp_plan_fibre_count", "spm_selftest_tc_rowpass")
 
 
 def library_path() -> str:
@@ -150,6 +150,8 @@ def load(build_if_missing: bool = False):
     lib.spm_selftest_mttkrp_timeout.restype = i32
     lib.spmttkrp_plan_fibre_count.argtypes = [P, i32, P]
     lib.spmttkrp_plan_fibre_count.restype = i32
+    lib.spm_selftest_tc_rowpass.argtypes = [i32, i64, P, P, P, P, P, P, P]
+    lib.spm_selftest_tc_rowpass.restype = i32
     lib.spmttkrp_noalloc_status.argtypes = [P]
     lib.spmttkrp_noalloc_status.restype = i32
     lib.spm_inject_alloc_failure.argtypes = [i32]
@@ -599,6 +601,27 @@ def spm_selftest_mttkrp_timeout(plan, mode: int, factors, out, stream=None) -> i
     return int(load().spm_selftest_mttkrp_timeout(plan.handle, int(mode), _ptrs(list(factors)),
                                                   ctypes.c_void_p(out.data_ptr()),
                                                   _stream(stream)))
+
+
+def spm_selftest_tc_rowpass(M, V, stream=None):
+    """The CP-ALS row passes of one mode on caller data: M (I x R float32
+    CUDA), V (R x R float64 CUDA, SPD).  Returns (Z, Y, G, lam): Z = M V^-1,
+    Y = Z / lam (float32), G = Y^T Y (float64; R = 16, 32 only, else zeros),
+    lam = column 2-norms of Z (float64)."""
+    import torch
+    I, R = M.shape
+    Z = torch.empty_like(M)
+    Y = torch.empty_like(M)
+    G = torch.zeros(R, R, dtype=torch.float64, device=M.device)
+    lam = torch.empty(R, dtype=torch.float64, device=M.device)
+    _check(load().spm_selftest_tc_rowpass(int(R), int(I), ctypes.c_void_p(M.data_ptr()),
+                                          ctypes.c_void_p(V.data_ptr()),
+                                          ctypes.c_void_p(Z.data_ptr()),
+                                          ctypes.c_void_p(Y.data_ptr()),
+                                          ctypes.c_void_p(G.data_ptr()),
+                                          ctypes.c_void_p(lam.data_ptr()), _stream(stream)),
+           "spm_selftest_tc_rowpass")
+    return Z, Y, G, lam
 
 
 def spmttkrp_noalloc_status(stream=None) -> int:

@@ -270,3 +270,76 @@ spm_status als_sweep(spmttkrp_plan_s* p, void* const* factors, double* lambda, d
 }
 
 }  // namespace spm
+
+using namespace spm;
+
+extern "C" spm_status spm_selftest_tc_rowpass(int R, int64_t I, const float* M, const double* V,
+                                              float* Z, float* Y, double* G, double* lambda,
+                                              void* stream) {
+  if (!(R == 16 || R == 32 || R == 64) || !tc_solve_rank(R)) return SPM_ERR_UNSUPPORTED;
+  if (I < 1 || !M || !V || !Z || !Y || !G || !lambda) return SPM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int cap = std::max(1, sm_count()) * 4;  // the plans' row-pass partial count
+  const size_t RR = (size_t)R * R;
+  spm_als_state A;
+  double* grams = nullptr;
+  int* err = nullptr;
+  spm_status st = SPM_OK;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (st == SPM_OK && cudaMalloc(p, bytes) != cudaSuccess) {
+      (void)cudaGetLastError();
+      st = SPM_ERR_OOM;
+    }
+  };
+  alloc((void**)&grams, sizeof(double) * 2 * RR);
+  alloc((void**)&err, sizeof(int));
+  alloc((void**)&A.chol, sizeof(double) * RR);
+  alloc((void**)&A.winv, sizeof(float) * 2 * RR);
+  alloc((void**)&A.wdig, als_wdig_bytes(R));
+  alloc((void**)&A.colsq_part, sizeof(double) * R * cap);
+  alloc((void**)&A.colmax_part, sizeof(float) * R * cap);
+  alloc((void**)&A.lambda_ws, sizeof(double) * 2 * R);
+  alloc((void**)&A.gram_part, sizeof(double) * RR * cap);
+  alloc((void**)&A.inner_part, sizeof(double) * R * cap);
+  if (st == SPM_OK) {
+    A.M = const_cast<float*>(M);
+    A.Z = Z;
+    A.gram_blocks = cap;
+    auto run = [&]() -> spm_status {
+      SPM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+      // V = the Hadamard product over the modes other than 0 of a two-mode "tensor": grams[1]
+      SPM_CUDA_TRY(cudaMemcpyAsync(grams + RR, V, sizeof(double) * RR, cudaMemcpyDeviceToDevice, s));
+      system_kernel<<<R, SYS_THREADS, 0, s>>>(grams, 2, 0, R, A.chol, A.winv, A.wdig, err);
+      const int nb = als_row_blocks(I, cap);
+      SPM_TRY(launch_solve(R, nb, A, I, err, nullptr, s));
+      const bool tcg = tc_gram_rank(R);
+      lambda_kernel<<<R, 32, 0, s>>>(A.colsq_part, A.colmax_part, nb, R, A.lambda_ws, err);
+      if (tcg) {
+        const int nbg = tc_gram_blocks(I, cap);
+        SPM_TRY(launch_tc_scale_gram(R, false, nbg, A, I, Y, false, err, nullptr, s));
+        gram_reduce_kernel<<<std::max(1, std::min(1024, R * R / 8)), 256, 0, s>>>(A.gram_part, nbg, R,
+                                                                                 G, err);
+      } else {
+        const int nbs = als_row_blocks(I, cap);
+        scale_kernel<float><<<nbs, ALS_THREADS, 0, s>>>(A.Z, A.lambda_ws, I, R, Y, nullptr,
+                                                         A.inner_part, err, nullptr);
+      }
+      SPM_CUDA_TRY(cudaMemcpyAsync(lambda, A.lambda_ws, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
+      SPM_CUDA_TRY(cudaGetLastError());
+      int h = 0;
+      SPM_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SPM_CUDA_TRY(cudaStreamSynchronize(s));
+      if (h & DEV_ERR_NUMERIC) return SPM_ERR_NUMERIC;
+      if (h & DEV_ERR_TIMEOUT) return SPM_ERR_TIMEOUT;
+      return SPM_OK;
+    };
+    st = run();
+  }
+  cudaStreamSynchronize(s);
+  for (void* p : {(void*)grams, (void*)err, (void*)A.chol, (void*)A.winv, (void*)A.wdig,
+                  (void*)A.colsq_part, (void*)A.colmax_part, (void*)A.lambda_ws,
+                  (void*)A.gram_part, (void*)A.inner_part})
+    if (p) cudaFree(p);
+  (void)cudaGetLastError();
+  return st;
+}
