@@ -930,18 +930,44 @@ __device__ __forceinline__ void mttkrp_fixup_body(const float* __restrict__ cta_
     const int r = lane + 32 * j;
     s[j] = r < R ? p1[r] : 0.f;
   }
-  for (int q = z + 1; q < kappa; ++q) {
-    const int* mq = cta_meta + 4 * q;
-    const int fq = mq[2];
-    if (fq & META_EMPTY) continue;
-    if (mq[0] != row) break;
-    const float* p0 = cta_part + (int64_t)(2 * q) * R;
+  // The partitions after z that continue `row`, in order; their metadata and
+  // partials are loaded FQ at a time ahead of the (ordered) additions, so a
+  // head row cut into many partitions does not pay one load latency each.
+  constexpr int FQ = 4;
+  bool more = true;
+  for (int q0 = z + 1; q0 < kappa && more; q0 += FQ) {
+    int4 mq[FQ];
+    float pq[FQ][8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int r = lane + 32 * j;
-      if (r < R) s[j] += p0[r];
+    for (int k = 0; k < FQ; ++k) {
+      const int q = q0 + k;
+      mq[k] = q < kappa ? *reinterpret_cast<const int4*>(cta_meta + 4 * q) : make_int4(-1, -1, 0, 0);
+      const float* p0 = cta_part + (int64_t)(2 * (q < kappa ? q : z)) * R;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int r = lane + 32 * j;
+        pq[k][j] = r < R ? p0[r] : 0.f;
+      }
     }
-    if (!(mq[1] == row && (fq & META_SHARED_NEXT))) break;
+#pragma unroll
+    for (int k = 0; k < FQ; ++k) {
+      if (!more || q0 + k >= kappa) {
+        more = false;
+        continue;
+      }
+      const int fq = mq[k].z;
+      if (fq & META_EMPTY) continue;
+      if (mq[k].x != row) {
+        more = false;
+        continue;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int r = lane + 32 * j;
+        if (r < R) s[j] += pq[k][j];
+      }
+      if (!(mq[k].y == row && (fq & META_SHARED_NEXT))) more = false;
+    }
   }
   float* dst = out + (int64_t)row * R;
 #pragma unroll
