@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batching", action="store_true",
                     help="skip the batching comparison that the headline line carries")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the short serving comparison that the headline line carries")
     ap.add_argument("--workload", default="scale",
                     choices=["scale", "batching", "serving", "precision", "five", "schemes",
                              "lean", "fibre", "probe"],
@@ -550,6 +552,24 @@ def main():
             "total_nnz": res["config"]["total_nnz"], "sweeps": res["config"]["sweeps"],
             "clocks": res["clocks"], "wall_s": round(res["wall_s"], 1)}
 
+    # and the serving comparison on the first SERVING_REQUESTS requests of the
+    # Poisson stream (p50/p99 time to solution, solves/s)
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        torch.cuda.empty_cache()
+        t_sv = time.perf_counter()
+        sv = serving_measure(SERVING_REQUESTS)
+        serving = {
+            "workload": f"first {SERVING_REQUESTS} requests of the seeded Poisson stream "
+                        "(200 requests/s; 3 or 4 modes, dims log-uniform [1e3, 1e6], nnz "
+                        "log-uniform [1e4, 5e7], R in {8, 16, 32, 64}), tol 1e-4, <= 50 sweeps",
+            "metric": "CPD solves/s + p50/p99 time to solution", "unit": "solves/s",
+            "served_bf16": sv["served_bf16_continuous_batching"],
+            "plain_fp32_per_tensor": sv["plain_fp32_per_tensor"],
+            "speedup_solves_per_s": sv["speedup_solves_per_s"],
+            "fit_agreement": sv["fit_agreement"], "total_nnz": sv["config"]["total_nnz"],
+            "clocks": sv["clocks"], "wall_s": round(time.perf_counter() - t_sv, 1)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -578,6 +598,7 @@ def main():
             "als_sweep_ms": als_ms,
             "plan_bytes": spm.spmttkrp_plan_bytes(plan),
             "batching": batching,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     plan.destroy()
@@ -1011,11 +1032,20 @@ def run_serving(args, rank, world):
         sweep until the same stopping rule).
     Time to solution = finish - arrival (host clock); solves/s = requests /
     (last finish - first arrival)."""
+    print(json.dumps(serving_measure(args.requests)), flush=True)
+
+
+SERVING_REQUESTS = 60  # the default line's serving comparison (the full workload: 200)
+
+
+def serving_measure(n_requests, with_clocks=True):
+    """The serving comparison of run_serving on the first n_requests of the
+    seeded request stream; returns its JSON line as a dict."""
     import numpy as np
     import torch
     import synth
     import paper_2503_18198_gb300 as spm
-    specs = synth.serving_specs(args.requests)
+    specs = synth.serving_specs(n_requests)
     tol, cap, budget = 1e-4, 50, 150 * 10**9
     reqs = []
     for t_arr, dims, nnz, R, seed in specs:
@@ -1026,8 +1056,9 @@ def run_serving(args, rank, world):
     torch.cuda.synchronize()
     n = len(reqs)
     total_nnz = sum(int(r[3].numel()) for r in reqs)
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
+    clocks = ClockSampler(torch.cuda.current_device()) if with_clocks else None
+    if clocks:
+        clocks.start()
 
     # ---- served: continuous batching, BF16 factors
     S = spm.Server(budget, max_active=256, flags=spm.SPM_FACTOR_BF16,
@@ -1082,7 +1113,7 @@ def run_serving(args, rank, world):
         plain[k] = ((time.perf_counter() - t0) - t_arr, sw, f)
         del fac
     plain_span = max(reqs[k][0] + plain[k][0] for k in plain) - reqs[0][0]
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
 
     def summary(d, span):
         tts = np.array([v[0] for v in d.values()]) * 1e3
@@ -1108,7 +1139,9 @@ def run_serving(args, rank, world):
         "fit_agreement": {"max_abs_dfit": float(dfit.max()) if dfit.size else None,
                           "within_1e-3": int((dfit <= 1e-3).sum()), "of": len(ok)},
         "clocks": clk}
-    print(json.dumps(line), flush=True)
+    del reqs
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_precision(args, rank, world):
