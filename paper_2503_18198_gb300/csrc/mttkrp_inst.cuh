@@ -9,6 +9,10 @@ namespace spm {
 
 using MttkrpKernelFn = void (*)(const MttkrpArgs);
 
+#ifndef SPM_MT_NARROW
+#define SPM_MT_NARROW 0
+#endif
+
 // Fast shapes: the rank is VEC * LPN * CPL with one 16-byte load per lane
 // and chunk.  Anything else uses the scalar variant (one nonzero per step).
 template <typename FT, int NIN, bool LEAN = false>
@@ -26,6 +30,14 @@ MttkrpKernelFn pick_mttkrp_t(int R) {
       }
     }
   }
+#if SPM_MT_NARROW
+  // FP32 rows of 32 or 64 ranks on half as many lanes, two 16-byte chunks
+  // per lane: twice the nonzeros per warp step
+  if constexpr (sizeof(FT) == 4 && NIN > 0) {
+    if (R == 8 * VEC) return &mttkrp_kernel<RI, NIN, FT, VEC, 4, 2, LEAN>;
+    if (R == 16 * VEC) return &mttkrp_kernel<RI, NIN, FT, VEC, 8, 2, LEAN>;
+  }
+#endif
   if (R % VEC == 0) {
     switch (R / VEC) {
       case 1: return &mttkrp_kernel<RI, NIN, FT, VEC, 1, 1, LEAN>;

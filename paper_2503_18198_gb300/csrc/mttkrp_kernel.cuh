@@ -97,6 +97,9 @@ enum : int {
 #ifndef SPM_MT_PAIRS_BF16
 #define SPM_MT_PAIRS_BF16 1  // 1: the same for BF16 factors (raw words widened to FP32 pairs)
 #endif
+#ifndef SPM_MT_U16
+#define SPM_MT_U16 1  // gather batch when a step's rows take 16 registers per lane
+#endif
 #ifndef SPM_MT_REUSE
 #define SPM_MT_REUSE 0  // 1: a slot keeps its first input mode's row and skips a repeated gather
 #endif
@@ -258,7 +261,7 @@ __device__ __forceinline__ void mttkrp_partition(const MttkrpArgs& a, const int 
   // lanes: the same two-step batch keeps them within 64 registers
   constexpr int U = NIN == 0 ? 1
                   : (VEC * (int)sizeof(FT) == 8 ? 2
-                     : (PIPE_REGS <= 4 ? 4 : (PIPE_REGS <= 8 ? 2 : 1)));
+                     : (PIPE_REGS <= 4 ? 4 : (PIPE_REGS <= 8 ? 2 : SPM_MT_U16)));
 #endif
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int next_unit;
