@@ -188,6 +188,9 @@ spm_status gram(spmttkrp_plan_s* p, const void* Y, int64_t I, double* G, cudaStr
 
 spm_status ensure_als_state(spmttkrp_plan_s* p) {
   spm_als_state& A = p->als;
+  if (!A.side) SPM_CUDA_TRY(cudaStreamCreateWithFlags(&A.side, cudaStreamNonBlocking));
+  if (!A.ev_fork) SPM_CUDA_TRY(cudaEventCreateWithFlags(&A.ev_fork, cudaEventDisableTiming));
+  if (!A.ev_join) SPM_CUDA_TRY(cudaEventCreateWithFlags(&A.ev_join, cudaEventDisableTiming));
   if (A.M) return SPM_OK;
   const int R = p->R;
   int64_t Imax = 1;
@@ -229,8 +232,19 @@ spm_status als_sweep(spmttkrp_plan_s* p, void* const* factors, double* lambda, d
   const int nb_solve = A.gram_blocks;
   for (int d = 0; d < N; ++d) {
     const int64_t I = p->dims[d];
+    // V, its Cholesky factor and V^-1 for mode d need the other modes'
+    // Grams (final once the previous mode's Gram is reduced, i.e. at this
+    // point of `s`), not M: they are formed on the side stream beside the
+    // MTTKRP, and the solve waits for them.  The fork also orders the
+    // previous mode's solve (the last reader of V^-1) before the overwrite.
+    SPM_CUDA_TRY(cudaEventRecord(A.ev_fork, s));
+    SPM_CUDA_TRY(cudaStreamWaitEvent(A.side, A.ev_fork, 0));
+    system_kernel<<<R, SYS_THREADS, 0, A.side>>>(A.gram, N, d, R, A.chol, A.winv, A.wdig,
+                                                 p->dev_err);
+    SPM_CUDA_TRY(cudaGetLastError());
+    SPM_CUDA_TRY(cudaEventRecord(A.ev_join, A.side));
     SPM_TRY(run_mttkrp(p, d, factors, A.M, s));
-    system_kernel<<<R, SYS_THREADS, 0, s>>>(A.gram, N, d, R, A.chol, A.winv, A.wdig, p->dev_err);
+    SPM_CUDA_TRY(cudaStreamWaitEvent(s, A.ev_join, 0));
     const int nb = als_row_blocks(I, nb_solve);
     // rows without nonzeros in mode d have a zero update: passes skip them
     const uint32_t* live = p->mode[d].empty_rows > 0 ? p->mode[d].rowmask : nullptr;

@@ -84,6 +84,9 @@ void free_plan(spmttkrp_plan_s* p) {
     if (e) cudaEventDestroy(e);
   if (p->copy_in) cudaStreamDestroy(p->copy_in);
   if (p->copy_out) cudaStreamDestroy(p->copy_out);
+  if (p->als.ev_fork) cudaEventDestroy(p->als.ev_fork);
+  if (p->als.ev_join) cudaEventDestroy(p->als.ev_join);
+  if (p->als.side) cudaStreamDestroy(p->als.side);
   for (int i = 0; i < p->nallocs; ++i) cudaFree(p->allocs[i]);
   (void)cudaGetLastError();
   delete p;
@@ -257,7 +260,7 @@ spm_status spmttkrp_plan_bytes_estimate(int nmodes, const int64_t* dims, int64_t
   if (fibre && (nmodes != 3 || fibre_slots(rank) == 0)) return SPM_ERR_UNSUPPORTED;
   size_t tr = 0;
   plan_bytes_estimate(nmodes, dims, nnz, rank, kappa, true, (flags & SPM_PLAN_LEAN) != 0, resident,
-                      &tr, fibre);
+                      &tr, fibre, (int)((flags & SPM_POLICY_MASK) >> 4));
   if (transient) *transient = tr;
   return SPM_OK;
 }

@@ -620,6 +620,19 @@ void partition_copy(spmttkrp_plan_s* p, int d, const int* rows, int64_t stride, 
   units_from_partitions_kernel<<<grid_for(P + 1, T), T, 0, s>>>(c.off, p->kappa, units, c.woff);
 }
 
+// Entries of the build's sort scratch: the nonzeros, or the rows of the
+// longest mode when some mode is partitioned by Scheme 1 (its rows are
+// sorted by degree); policy is SPM_POLICY_* >> 4.
+int64_t sort_capacity(int N, const int64_t* dims, int64_t nn, int policy, int kappa) {
+  int64_t rows = 0;
+  for (int w = 0; w < N; ++w) {
+    const bool scheme1 = policy == (int)(SPM_POLICY_SCHEME1 >> 4) ||
+                         (policy == (int)(SPM_POLICY_ADAPTIVE >> 4) && dims[w] >= kappa);
+    if (scheme1) rows = std::max(rows, dims[w]);
+  }
+  return std::max(nn, rows);
+}
+
 template <int RI>
 spm_status build_copies_t(spmttkrp_plan_s* p, const int32_t* const* idx_in, const float* vals,
                           cudaStream_t s) {
@@ -636,9 +649,9 @@ spm_status build_copies_t(spmttkrp_plan_s* p, const int32_t* const* idx_in, cons
   SortScratch sc;
   int64_t* d_dims = nullptr;
   const int64_t nn = n > 0 ? n : 1;
-  int64_t Imax = 1;
-  for (int w = 0; w < N; ++w) Imax = std::max(Imax, p->dims[w]);
-  const int64_t cap = std::max(nn, Imax);
+  // the keys, payloads and histograms hold nnz entries, or I_d entries where
+  // Scheme 1 sorts the rows of a mode by degree
+  const int64_t cap = sort_capacity(N, p->dims, nn, p->policy, p->kappa);
   const int nblocks_max = (int)ceil_div<int64_t>(cap, RS_TILE);
   SPM_CUDA_TRY(cudaMallocAsync((void**)&k64a, sizeof(unsigned long long) * cap, s));
   SPM_CUDA_TRY(cudaMallocAsync((void**)&k64b, sizeof(unsigned long long) * cap, s));
@@ -836,7 +849,7 @@ spm_status build_copies_t(spmttkrp_plan_s* p, const int32_t* const* idx_in, cons
 }  // namespace
 
 void plan_bytes_estimate(int N, const int64_t* dims, int64_t nnz, int R, int kappa, bool als,
-                         bool lean, size_t* resident, size_t* transient, bool fibre) {
+                         bool lean, size_t* resident, size_t* transient, bool fibre, int policy) {
   // mirrors the plan_alloc calls of spmttkrp_plan, build_copies and
   // ensure_als_state (each allocation of 0 bytes counts 16)
   const int RI = record_int4s(N);
@@ -873,7 +886,7 @@ void plan_bytes_estimate(int N, const int64_t* dims, int64_t nnz, int R, int kap
   }
   *resident = b;
   // stream-ordered scratch of the build (keys, payloads, histograms)
-  const int64_t cap = std::max(nn, Imax);
+  const int64_t cap = sort_capacity(N, dims, nn, policy, kappa);
   *transient = sizeof(unsigned long long) * 2 * (size_t)cap + sizeof(int32_t) * 2 * (size_t)cap +
                sizeof(uint32_t) * RS_BINS * (size_t)ceil_div<int64_t>(cap, RS_TILE) +
                sizeof(uint32_t) * RS_BINS + sizeof(int64_t) * SPM_MAX_MODES +

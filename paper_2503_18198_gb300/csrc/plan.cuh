@@ -52,6 +52,10 @@ struct spm_als_state {
   double* lambda_ws = nullptr;        // R
   float* M = nullptr;                 // Imax*R MTTKRP output
   float* Z = nullptr;                 // Imax*R unnormalised update
+  // the normal-equation systems of mode d depend only on the other modes'
+  // Grams, so they are formed on a side stream while the MTTKRP of mode d runs
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 struct spmttkrp_plan_s {
@@ -123,7 +127,8 @@ inline int fibre_slots(int R) {
 // with `als` the CP-ALS state) and the most its build adds for a while
 // (transient scratch), for the given shape.
 void plan_bytes_estimate(int N, const int64_t* dims, int64_t nnz, int R, int kappa, bool als,
-                         bool lean, size_t* resident, size_t* transient, bool fibre = false);
+                         bool lean, size_t* resident, size_t* transient, bool fibre = false,
+                         int policy = 0);
 
 // P2 again for a new partition count (cost-balanced and Scheme 2 policies).
 spm_status plan_repartition(spmttkrp_plan_s* p, int kappa, cudaStream_t s);

@@ -66,3 +66,19 @@ def test_default_partition_count_needs_a_device():
     with pytest.raises(spm.SpmError) as e:
         binding.spmttkrp_plan_bytes_estimate((100, 100, 100), 1000, 8, 0)
     assert e.value.status == CUDA
+
+
+def test_sort_scratch_follows_the_nonzeros_unless_rows_are_sorted():
+    # a long mode with few nonzeros: the default policy sorts nonzeros only,
+    # Scheme 1 (and the adaptive rule on a mode of >= kappa rows) also sorts
+    # the rows of the longest such mode by degree
+    dims, nnz = (1_000_000, 300, 200), 10_000
+    small = est(dims, nnz, 16)[1]
+    assert small < 40 * nnz  # keys, payloads and histograms of 10,000 entries
+    for policy in (binding.SPM_POLICY_SCHEME1, binding.SPM_POLICY_ADAPTIVE):
+        big = est(dims, nnz, 16, flags=policy)[1]
+        assert big >= 24 * dims[0]  # two 64-bit keys and two 32-bit payloads per row
+    # the adaptive rule picks Scheme 2 for every mode shorter than kappa
+    assert est((200, 300, 250), nnz, 16, flags=binding.SPM_POLICY_ADAPTIVE)[1] == \
+        est((200, 300, 250), nnz, 16)[1]
+    assert est(dims, nnz, 16, flags=binding.SPM_POLICY_SCHEME2)[1] == small
