@@ -231,6 +231,9 @@ spm_status batch_add(spm_batch_s* B, spmttkrp_plan_s* p, void* const* factors, d
     if (p->mode[d].scheme == 1) return SPM_ERR_UNSUPPORTED;
   for (int w = 0; w < p->N; ++w)
     if (!factors[w] || (reinterpret_cast<uintptr_t>(factors[w]) & 15u)) return SPM_ERR_INVALID_ARG;
+  if (!B->side) SPM_CUDA_TRY(cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking));
+  if (!B->ev_fork) SPM_CUDA_TRY(cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming));
+  if (!B->ev_join) SPM_CUDA_TRY(cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming));
   for (const spmttkrp_plan_s* q : B->plans)
     if (q == p) return SPM_ERR_INVALID_ARG;  // one batch slot per plan (shared workspace)
   // the members' convergence state lives on the device between sweeps
@@ -444,8 +447,21 @@ spm_status batch_sweep(spm_batch_s* B, cudaStream_t s) {
   const int2* it = B->items;
   for (int d = 0; d < B->maxN; ++d) {
     const spm_batch_s::ModeItems& I = B->mi[d];
+    // each member's system for mode d needs its other modes' Grams (final at
+    // this point of `s`), not its MTTKRP: formed on the side stream beside
+    // the MTTKRP launches; the fork also orders the previous mode's solve
+    // before V^-1 is overwritten
+    const bool fork = B->side && B->ev_fork && B->ev_join;
+    cudaStream_t ss = fork ? B->side : s;
+    if (fork) {
+      SPM_CUDA_TRY(cudaEventRecord(B->ev_fork, s));
+      SPM_CUDA_TRY(cudaStreamWaitEvent(B->side, B->ev_fork, 0));
+    }
+    batch_system_kernel<<<I.n_tens, SYS_THREADS, 0, ss>>>(B->bt, it + I.tens_off, d);
+    SPM_CUDA_TRY(cudaGetLastError());
+    if (fork) SPM_CUDA_TRY(cudaEventRecord(B->ev_join, B->side));
     SPM_TRY(batch_mttkrp(B, d, s));
-    batch_system_kernel<<<I.n_tens, SYS_THREADS, 0, s>>>(B->bt, it + I.tens_off, d);
+    if (fork) SPM_CUDA_TRY(cudaStreamWaitEvent(s, B->ev_join, 0));
     if (I.n_solve > 0) batch_solve_kernel<<<I.n_solve, ALS_THREADS, 0, s>>>(B->bt, it + I.solve_off, d);
     for (int k = 0; k < 3; ++k)
       if (I.n_tcs[k] > 0) SPM_TRY(launch_batch_tc_solve(16 << k, B->bt, it + I.tcs_off[k], I.n_tcs[k], d, s));
@@ -479,6 +495,9 @@ void batch_free(spm_batch_s* B) {
   if (B->bt) cudaFree(B->bt);
   if (B->items) cudaFree(B->items);
   if (B->queue) cudaFree(B->queue);
+  if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+  if (B->ev_join) cudaEventDestroy(B->ev_join);
+  if (B->side) cudaStreamDestroy(B->side);
   (void)cudaGetLastError();
   delete B;
 }

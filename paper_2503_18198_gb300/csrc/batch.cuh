@@ -38,6 +38,10 @@ struct spm_batch_s {
   size_t mtt_smem[spm::KC_NONE] = {};
   size_t smem_set[spm::KC_NONE] = {};  // dynamic shared memory the attribute allows
   std::vector<int2> stage;
+  // side stream on which each mode's systems are formed beside its MTTKRP
+  // (created when the first member is added, outside any stream capture)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace spm {
