@@ -319,7 +319,12 @@ spm_status spmttkrp_run_all_host(spmttkrp_plan_t plan, const void *const *host_f
  * spmttkrp_plan_status reports SPM_ERR_NUMERIC and clears the flag (the
  * check is device-side, so it is seen at the next synchronising call).
  * The CP-ALS state is the factors and lambda, both the caller's: a run
- * resumed from copies of them continues bitwise as the uninterrupted one. */
+ * resumed from copies of them continues bitwise as the uninterrupted one.
+ * Stream order: V and its inverse for mode d need no MTTKRP output, so they
+ * are formed on a side stream owned by the plan, forked from `stream` with
+ * an event and joined back into it before the solve of mode d; work queued
+ * on `stream` after the call sees the whole sweep.  Calls on one plan from
+ * different streams must not overlap (they share the plan's workspace). */
 spm_status cpd_als_step(spmttkrp_plan_t plan, void *const *factors,
                         double *lambda, double *fit, void *stream);
 
@@ -394,7 +399,9 @@ spm_status spm_batch_create(spm_batch_t *out, int ntensors,
 
 /* One sweep over every still-active tensor.  Launch-only (no host
  * synchronisation, no allocation): can be captured in a CUDA graph and
- * replayed. */
+ * replayed.  Each mode's systems are formed on a side stream of the batch
+ * (created when the first tensor is added), forked from and joined back
+ * into `stream` with events, so a capture on `stream` records them too. */
 spm_status spm_batch_sweep(spm_batch_t batch, void *stream);
 
 /* Synchronise `stream`; active[t] (host) = 1 while tensor t still iterates,
