@@ -543,7 +543,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(dims, idx, vals, Y, R, args.cpu_seconds)
 
-    # the benchmark spec's second target beside the headline: BF16 batched CP-ALS
+    # the batching comparison beside the headline: BF16 batched CP-ALS
     # against the tuned plain per-tensor FP32 path on the 512-tensor workload
     batching = None
     if rank == 0 and world == 1 and not args.no_batching:
