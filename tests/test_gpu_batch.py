@@ -37,6 +37,10 @@ MIX = [
     ((500, 400, 9, 3), 30000, 64, 6),
     ((33, 17, 65), 2000, 32, 7),
     ((120, 90, 60, 4), 15000, 16, 8),
+    # first modes of tens of thousands of rows: many virtual row blocks in
+    # every row pass of that mode, a handful in the others
+    ((40000, 60, 30), 50000, 16, 9),
+    ((36000, 50, 3000), 60000, 32, 10),
 ]
 
 
@@ -149,6 +153,25 @@ def test_batch_matches_oracle_fit_and_factors():
     ofac, olam, ofit = oracle.cpd_als(dims, idx, vals, Y0, 2, prec="fp32")
     assert abs(B.fits[0].item() - ofit[-1]) < 1e-3
     for w in range(4):
+        g = fac[w].double().cpu().numpy()
+        assert np.linalg.norm(g - ofac[w]) / np.linalg.norm(ofac[w]) < 1e-4
+    lam = B.lam(0).cpu().numpy()
+    assert np.linalg.norm(lam - olam) / np.linalg.norm(olam) < 1e-4
+
+
+@pytest.mark.parametrize("dims,nnz,R,seed", [MIX[8], MIX[9]])
+def test_long_mode_members_match_oracle(dims, nnz, R, seed):
+    """Members with a first mode of tens of thousands of rows (its row passes
+    split over many virtual blocks, the other modes' over a few) after two
+    batched sweeps, against the oracle's CP-ALS (Sec. II-A5) on the same FP32
+    factors."""
+    plan, idx, vals = make_plan(dims, nnz, R, seed)
+    Y0 = synth.factors(dims, R, seed=100 + seed)
+    fac = [torch.as_tensor(f).cuda().contiguous() for f in Y0]
+    B, _, _ = batch_run([plan], [fac], 2)
+    ofac, olam, ofit = oracle.cpd_als(dims, idx, vals, Y0, 2, prec="fp32")
+    assert abs(B.fits[0].item() - ofit[-1]) < 1e-3
+    for w in range(3):
         g = fac[w].double().cpu().numpy()
         assert np.linalg.norm(g - ofac[w]) / np.linalg.norm(ofac[w]) < 1e-4
     lam = B.lam(0).cpu().numpy()
